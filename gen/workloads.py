@@ -1,0 +1,75 @@
+"""Named synthetic workloads (seeded; seed = 1000 * workload + instance).
+
+* ``line10``: 10-qubit line brickwork, depth 8, Haar SU(2) + CZ, cut into
+  two 6-qubit subcircuits by 2 wire cuts; exact FP64 tensors.  Plain
+  brickwork would cross the (4,5) boundary in four layers; the reading used
+  here keeps that coupler in layer 4 only, so qubit 5's wire moves into the
+  left subcircuit for that one gate and back (2 cuts, widths 6/6, 5 outputs
+  each).
+* ``grid30``: the shape of a 30-qubit (5x6) grid cut into 4 subcircuits of
+  width 10 with 10 cuts -- a shape-matched network with pseudo-physical
+  tensors (a real 5x6 depth-10 grid needs far more than 10 cuts at width 10).
+* ``small_random``: tiny exact cut circuits for parity and oracle pins.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import circuits, cutter, statevector as sv, tensors
+from .network import Network
+
+
+def line_with_boundary(n: int, depth: int, seed: int, boundary: int, keep_layers):
+    """Line brickwork whose coupler (boundary-1, boundary) is kept only in ``keep_layers``."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    gates = []
+    for layer in range(depth):
+        for q in range(n):
+            gates.append(("u", (q,), sv.haar_su2(rng)))
+        for q in range(layer % 2, n - 1, 2):
+            if q == boundary - 1 and layer not in keep_layers:
+                continue
+            gates.append(("cz", (q, q + 1), sv.CZ))
+    return n, gates
+
+
+def line10(instance: int = 0):
+    """Returns (network, (n, gates)) for the 10-qubit, 2-cut workload."""
+    n, gates = line_with_boundary(10, 8, 1000 * 1 + instance, boundary=5, keep_layers=(4,))
+    part = cutter.contiguous_partition(n, gates, [list(range(5)), list(range(5, 10))])
+    cc = cutter.cut_circuit(n, gates, part)
+    assert cc.n_cuts == 2 and cutter.widths(cc) == [6, 6], (cc.n_cuts, cutter.widths(cc))
+    net = tensors.exact_network(cc)
+    net.meta.update({"workload": "line10", "circuit": "line brickwork n=10 depth=8"})
+    return net, (n, gates)
+
+
+def grid30(instance: int = 0) -> Network:
+    net = tensors.shape_matched_network(30, 4, 10, 10, seed=1000 * 2 + instance, max_node_cuts=7)
+    net.meta.update({"workload": "grid30", "circuit": "shape of 5x6 grid, 4 subcircuits, width 10, 10 cuts"})
+    return net
+
+
+def random_cut_circuit(seed: int, n: int, depth: int, n_sub: int, family: str = "line"):
+    """A small random circuit cut into ``n_sub`` contiguous qubit groups."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    if family == "line":
+        n, gates = circuits.line(n, depth, seed)
+    else:
+        raise ValueError(family)
+    # random contiguous group boundaries
+    cuts_at = sorted(rng.choice(np.arange(1, n), size=n_sub - 1, replace=False))
+    bounds = [0] + list(cuts_at) + [n]
+    groups = [list(range(bounds[i], bounds[i + 1])) for i in range(n_sub)]
+    part = cutter.contiguous_partition(n, gates, groups)
+    cc = cutter.cut_circuit(n, gates, part)
+    return cc, (n, gates)
+
+
+def small_exact(seed: int, n: int = 6, depth: int = 3, n_sub: int = 2, max_cuts: int = 8):
+    """Exact network from a random line circuit; redraws until <= max_cuts cuts."""
+    for k in range(100):
+        cc, circ = random_cut_circuit(seed * 101 + k, n, depth, n_sub)
+        if 0 < cc.n_cuts <= max_cuts:
+            return tensors.exact_network(cc), circ
+    raise RuntimeError("small_exact: no circuit within the cut limit")
