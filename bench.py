@@ -1,0 +1,346 @@
+#!/usr/bin/env python
+"""Reconstruction throughput on one GB300 (or N, one process per GPU).
+
+Workload: the 30-qubit grid shape -- 4 subcircuits of width 10, 10 cuts,
+pseudo-physical FP64 tensors, every qubit free (the full 2^30 FP32
+probability vector).  One step = one tqc_contract of the whole path (ingest,
+the pairwise steps, total mass Z, renormalisation) with the inputs resident
+in HBM.  Metric: reconstructed probabilities per second, for the chosen form
+(tensor-core split BF16, FP32 accumulate) and, beside it, the plain FP32
+CUDA-core form.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank reconstructs its own network instance (weak
+scaling, no collective on the data path); rank 0 prints one JSON line.
+`--impl reference` times the CPU FP64 oracle on the host cores instead."""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "reconstructed probs/s & % of roofline, chosen vs plain FP32 form at <=1e-5 err"
+UNIT = "probs/s"
+WORKLOAD = "grid30: 30 qubits, 4 subcircuits of width 10, 10 cuts, full 2^30 output"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="auto")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return p["hbm_gbs"], p["bf16_tflops"], p.get("bf16_tflops_sustained"), "measured"
+    except Exception:
+        return 6800.0, 1900.0, 1700.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.path = tempfile.mktemp(suffix=".csv")
+        self.proc = None
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(gpu_index)], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9 and parts[1].replace(".", "").isdigit():
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(rows[0][2]), "samples": len(rows),
+                "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit()),
+                "reasons": reasons}
+
+
+def step_bytes(st, out_bytes):
+    """Algorithmic HBM bytes of one pairwise step: operands read once, the
+    result written once."""
+    m, n, k = 2 ** st["log2_m"], 2 ** st["log2_n"], 2 ** st["log2_k"]
+    ein = {"bf16": 2, "bf16x3": 4, "tf32": 4}.get(st["prec"], 4) if st["class"] == "tcgen05" else 4
+    return ein * (m * k + n * k) + out_bytes * m * n
+
+
+def step_flops(st):
+    m, n, k = 2 ** st["log2_m"], 2 ** st["log2_n"], 2 ** st["log2_k"]
+    mult = 3 if (st["class"] == "tcgen05" and st["prec"] == "bf16x3") else 1
+    return 2.0 * m * n * k * mult
+
+
+def traffic_record(kernel):
+    """dram read+write bytes per launch from the committed ncu summary, or
+    None when the kernel source changed since the capture."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", f"{kernel}_traffic.md")
+    src = os.path.join(ROOT, "paper_2502_03445_gb300", "csrc", "umma.cu" if kernel.startswith("umma") else "simt.cu")
+    try:
+        rec = {}
+        with open(path) as f:
+            for line in f:
+                if ":" in line and line.startswith("- "):
+                    k, v = line[2:].split(":", 1)
+                    rec[k.strip()] = v.strip()
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        if rec.get("source_sha256_16") != h:
+            return None
+        return float(rec["dram_bytes_per_full_launch"])
+    except Exception:
+        return None
+
+
+def cpu_oracle_sample(net, target_s=12.0, seed=7):
+    import oracle
+    rng = np.random.Generator(np.random.PCG64(seed))
+    n = net.n_qubits
+    calib = [int(x) for x in rng.integers(0, 1 << n, size=16, dtype=np.int64)]
+    _, t = oracle.timed_sample(net, calib)
+    per = max(t / len(calib), 1e-6)
+    cnt = int(min(max(target_s / per, 16), 1 << 16))
+    states = [int(x) for x in rng.integers(0, 1 << n, size=cnt, dtype=np.int64)]
+    p, t = oracle.timed_sample(net, states)
+    return {"value": len(states) / t, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
+            "sample": f"{len(states)} uniformly drawn states of the grid30 network, oracle A "
+                      f"(4^10 cut assignments x 4 subcircuits per state), {t:.1f} s"}, states, p
+
+
+def run_reference(args):
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    from gen import workloads
+    net = workloads.grid30(0)
+    rng = np.random.Generator(np.random.PCG64(11))
+    per_step = 512
+    n = net.n_qubits
+    for _ in range(args.warmup):
+        oracle.recon_states(net, [int(x) for x in rng.integers(0, 1 << n, size=32, dtype=np.int64)])
+    times = []
+    for _ in range(args.steps):
+        st = [int(x) for x in rng.integers(0, 1 << n, size=per_step, dtype=np.int64)]
+        t0 = time.perf_counter()
+        oracle.recon_states(net, st)
+        times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    value = per_step * args.steps / tot
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "step": f"{per_step} sampled states"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
+                             "sample": f"{per_step} random states per step, oracle A (FP64 brute force over "
+                                       f"4^10 cut assignments)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def time_plan(torch, plan, out, steps, warmup, profile=False):
+    for _ in range(warmup):
+        plan.contract(out)
+    torch.cuda.synchronize()
+    if profile:
+        plan.profile(True)
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s.record()
+    for _ in range(steps):
+        plan.contract(out)
+    e.record()
+    torch.cuda.synchronize()
+    return s.elapsed_time(e) / steps
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    ws, rank, local = dist_env()
+    import torch
+    import torch.distributed as dist
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from gen import workloads
+    from paper_2502_03445_gb300 import tqc
+
+    net = workloads.grid30(rank)          # weak scaling: one independent network per rank
+    h = tqc.Network(net)
+    plan = tqc.Plan(h, precision=args.precision)
+    desc = plan.describe()
+    out = torch.empty(plan.out_elems, dtype=torch.float32, device="cuda")
+    probs_per_step = plan.out_elems
+
+    # warm up (allocates the workspace), then sample clocks around the timed region
+    for _ in range(max(args.warmup, 3)):
+        plan.contract(out)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    t_end = time.time() + 0.6          # load the GPU for a while so the sampler sees it
+    while time.time() < t_end:
+        plan.contract(out)
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    plan.profile(True)
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s.record()
+    for _ in range(args.steps):
+        plan.contract(out)
+    e.record()
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    ms = s.elapsed_time(e) / args.steps
+    clocks = sampler.stop() if sampler else None
+    if ws > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = probs_per_step * ws / (ms / 1e3)
+
+    # dominant kernel: the step with the largest mean duration over the timed region
+    hbm, bf16, bf16_sus, peak_kind = peaks()
+    step_ms = [plan.step_time(i)[0] for i in range(len(desc["steps"]))]
+    plan.profile(False)
+    top = int(np.argmax(step_ms))
+    st = desc["steps"][top]
+    out_b = 4
+    byt, fl = step_bytes(st, out_b), step_flops(st)
+    t_top = step_ms[top] / 1e3
+    ridge = bf16 * 1e12 / (hbm * 1e9)
+    kern = "umma_step" if st["class"] == "tcgen05" else "simt_step"
+    if fl / byt < ridge or st["class"] != "tcgen05":
+        roof = {"bound": "hbm", "achieved": byt / t_top / 1e9, "peak": hbm, "unit": "GB/s",
+                "peak_kind": f"{peak_kind} copy bandwidth"}
+    else:
+        roof = {"bound": "tensor", "achieved": fl / t_top / 1e12, "peak": bf16, "unit": "TFLOP/s",
+                "peak_kind": f"{peak_kind} bf16 burst"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = traffic_record(f"{kern}_grid30") if top == len(desc["steps"]) - 1 else None
+    roof["kernel"] = f"{kern} (step {top}: log2 M,N,K = {st['log2_m']},{st['log2_n']},{st['log2_k']})"
+    roof["algorithmic_bytes_per_launch"] = byt
+    roof["mean_launch_ms"] = step_ms[top]
+    roof["step_ms"] = step_ms
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": desc["precision"], "data": "synthetic",
+            "config": {"workload": WORKLOAD, "plan": [[s_["log2_m"], s_["log2_n"], s_["log2_k"], s_["class"]]
+                                                      for s_ in desc["steps"]],
+                       "order": desc["order"], "instance_seed": "2000 + rank",
+                       "l2": "working set 4.6 GB > 129 MB L2, no flush needed",
+                       "parallelism": f"weak x{ws}, one network per GPU"},
+            "roofline": roof, "gpu_launches": desc["launches_per_contract"] * args.steps,
+            "clocks": clocks}
+
+    # plain FP32 CUDA-core form on the same network
+    if not args.no_plain:
+        pplan = tqc.Plan(h, precision="fp32")
+        pms = time_plan(torch, pplan, out, max(2, min(args.steps, 5)), 2)
+        line["plain_fp32"] = {"value": probs_per_step / (pms / 1e3), "ms_per_step": pms,
+                              "speedup_of_chosen": pms / ms}
+        plain_out = out.clone()
+        plan.contract(out)
+        torch.cuda.synchronize()
+        tv = 0.5 * (out.double() - plain_out.double()).abs().sum().item()
+        line["plain_fp32"]["tv_chosen_vs_plain_full_vector"] = tv
+        del plain_out
+        pplan.close()
+    else:
+        plan.contract(out)
+        torch.cuda.synchronize()
+
+    # accuracy of the chosen form against the oracle on sampled states (rank 0)
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu, states, want = cpu_oracle_sample(net)
+        line["cpu_baseline"] = cpu
+        got = out.cpu().numpy()[np.array(states, dtype=np.int64)].astype(np.float64)
+        err = np.abs(got - want)
+        line["error_vs_oracle"] = {"states": len(states), "max_abs": float(err.max()),
+                                   "max_abs_rel_to_max_p": float(err.max() / np.abs(want).max()),
+                                   "tv_estimate": float(0.5 * err.mean() * probs_per_step)}
+
+    # end to end through the C ABI with host buffers: H2D of the tensors, D2H of the bin
+    if not args.no_e2e:
+        hin = [torch.from_numpy(np.ascontiguousarray(nd.data)).pin_memory() for nd in net.nodes]
+        hout = torch.empty(plan.out_elems, dtype=torch.float32).pin_memory()
+        plan.contract_host(hin, hout)
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            plan.contract_host(hin, hout)
+        t_e2e = (time.perf_counter() - t0) / args.e2e_steps
+        if ws > 1:
+            t = torch.tensor([t_e2e], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            t_e2e = float(t.item())
+        line["e2e"] = {"value": probs_per_step * ws / t_e2e, "unit": UNIT,
+                       "h2d_bytes_per_step": int(sum(x.numel() * 8 for x in hin)),
+                       "d2h_bytes_per_step": int(hout.numel() * 4), "ms_per_step": 1e3 * t_e2e}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    plan.close()
+    h.close()
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,234 @@
+/*
+ * tqc.h -- C ABI of the GB300 cut-network reconstruction library (libtqc.so).
+ *
+ * What the library computes (Eq. reconstruction, §II-A, and its tensor-network
+ * form, §III-B): given the m subcircuit output tensors of a cut circuit, each
+ * indexed by its output bits (dimension 2) and its cut edges (dimension 4,
+ * basis order I, X, Y, Z), the uncut circuit's output probabilities
+ *
+ *     P(x) = 2^{-|E|} sum_{e in {I,X,Y,Z}^{|E|}} prod_j T_j[e|E_j][x|out_j]
+ *
+ * for every state x of a requested bin, by a sequence of m-1 pairwise
+ * contractions (§III-B, Fig. subcircuit_contraction) in an order chosen by a
+ * planner (§III-E-1), with index slicing when tensors exceed a memory budget
+ * (§III-E-2).  The factor 1/2 per cut is applied once, exactly, at the end.
+ *
+ * Conventions
+ *   - Qubit q of a state is bit q of its index (little-endian); n_qubits <= 128.
+ *   - A bin fixes some qubits to given bits and leaves F qubits free.  Output
+ *     entry i (0 <= i < 2^F) is the state whose i-th free qubit (free qubits in
+ *     ascending order) carries bit i of the index; F <= 40.
+ *   - All errors are returned as tqc_status; no C++ exception crosses the ABI.
+ *     tqc_last_error() returns a thread-local message describing the last
+ *     failure on the calling thread (naming the offending subcircuit or cut for
+ *     validation errors).
+ *   - Device work is stream-ordered on the caller's stream.  After the first
+ *     tqc_contract on a plan (which allocates the plan's workspace), further
+ *     calls with z_out == NULL neither allocate nor synchronise.
+ *   - Handles are not thread-safe: one thread uses a plan at a time.
+ */
+#ifndef TQC_H_
+#define TQC_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define TQC_API __attribute__((visibility("default")))
+#else
+#define TQC_API
+#endif
+
+typedef struct tqc_net *tqc_net_t;
+typedef struct tqc_plan *tqc_plan_t;
+
+typedef enum {
+    TQC_OK = 0,
+    TQC_ERR_INVALID = 1,      /* bad argument, label or layout */
+    TQC_ERR_OOM = 2,          /* device or host allocation failed, or budget too small */
+    TQC_ERR_CUDA = 3,         /* a CUDA call failed (message holds cudaGetErrorString) */
+    TQC_ERR_TIMEOUT = 4,      /* a bounded device-side wait gave up */
+    TQC_ERR_UNSUPPORTED = 5   /* valid request outside what this build supports */
+} tqc_status;
+
+/* element types of tensors and outputs */
+enum { TQC_F64 = 0, TQC_F32 = 1 };
+
+/* arithmetic form of the pairwise contractions */
+enum {
+    TQC_PREC_FP32 = 0,   /* plain form: every step on CUDA cores in FP32 */
+    TQC_PREC_TF32 = 1,   /* dense steps on tcgen05 tensor cores, TF32 inputs, FP32 accumulate */
+    TQC_PREC_BF16 = 2,   /* dense steps on tcgen05, BF16 inputs, FP32 accumulate */
+    TQC_PREC_BF16X3 = 3, /* dense steps on tcgen05, split BF16 (hi*hi + hi*lo + lo*hi), FP32 accumulate */
+    TQC_PREC_AUTO = 4    /* library's choice (currently BF16X3) */
+};
+
+/* contraction-order search (§III-E-1) */
+enum {
+    TQC_PLANNER_GREEDY = 0,      /* greedy pairwise merge on the predicted step time */
+    TQC_PLANNER_EXHAUSTIVE = 1,  /* every contraction tree (m <= 9), best predicted time */
+    TQC_PLANNER_LEARNED = 2,     /* candidates ranked by the learned MLP cost model */
+    TQC_PLANNER_AUTO = 3         /* exhaustive for m <= 8, else greedy */
+};
+
+/* plan flags */
+enum {
+    TQC_FLAG_NO_RENORM = 1       /* skip division by the total mass Z (Z still reported) */
+};
+
+/*
+ * One subcircuit tensor in the Pauli basis (§II-A: p_j^{e}, §III-B: a tensor
+ * with one index per cut edge).
+ *   n_out, out_qubits : bit k of the output index x is original qubit out_qubits[k]
+ *   n_cut, cut_ids    : tensor axis d is cut edge cut_ids[d] (dim 4, order I,X,Y,Z);
+ *                       cut ids of a network are 0..n_cuts-1, each used by exactly
+ *                       two subcircuits
+ *   cut_role          : per axis, 0 = this subcircuit measures the cut (upstream),
+ *                       1 = it initialises the cut (downstream)
+ *   dtype, data       : TQC_F64 or TQC_F32 host array, row-major
+ *                       [c_0][c_1]...[c_{n_cut-1}][x], 4^n_cut * 2^n_out elements;
+ *                       data == NULL for every subcircuit makes a shape-only
+ *                       network (planning only, no device memory).
+ */
+typedef struct {
+    int32_t n_out;
+    const int32_t *out_qubits;
+    int32_t n_cut;
+    const int32_t *cut_ids;
+    const int8_t *cut_role;
+    int32_t dtype;
+    const void *data;
+} tqc_subcircuit;
+
+/*
+ * Validate the labels and build the network.  With data, copies every tensor
+ * to the current CUDA device (synchronously); the caller keeps ownership of
+ * its host arrays.  Fails with TQC_ERR_INVALID if output qubits do not
+ * partition 0..n_qubits-1, if a cut id is out of range, appears other than
+ * once upstream and once downstream, or joins a subcircuit to itself.
+ */
+TQC_API tqc_status tqc_network_create(int32_t n_qubits, int32_t n_sub, const tqc_subcircuit *subs,
+                                      tqc_net_t *out);
+
+/*
+ * Replace the tensor data of subcircuit `sub` (same shape) from host memory,
+ * stream-ordered on `cuda_stream` (asynchronous when host_data is pinned).
+ * The network must have been created with data.
+ */
+TQC_API tqc_status tqc_network_upload(tqc_net_t net, int32_t sub, int32_t dtype, const void *host_data,
+                                      void *cuda_stream);
+
+/* Free the network's device copies.  Plans made from it must be destroyed first. */
+TQC_API tqc_status tqc_destroy(tqc_net_t net);
+
+typedef struct {
+    int32_t use_free_mask;               /* 0 = every qubit free; 1 = the masks name the free
+                                            qubits (none set = a single state) */
+    uint64_t free_mask_lo, free_mask_hi; /* free qubits (bit q of lo = qubit q, of hi = q+64) */
+    const uint8_t *fixed_bits;           /* n_qubits bytes, bit value of each non-free qubit;
+                                            NULL = all zero; copied by tqc_plan */
+    int32_t precision;                   /* TQC_PREC_* */
+    int32_t planner;                     /* TQC_PLANNER_* */
+    uint64_t mem_budget_bytes;           /* device bytes for operands, intermediates and the
+                                            FP64 slice sum; 0 = unlimited */
+    const char *costmodel_path;          /* learned cost model file (TQC_PLANNER_LEARNED) */
+    int32_t autotune;                    /* 1 = time candidate tiles on first contract */
+    int32_t n_order;                     /* optional forced contraction order: n_order pairs */
+    const int32_t *order;                /* (a, b) per step; leaves are 0..m-1, step s makes m+s */
+    int32_t n_sliced;                    /* optional forced sliced cuts (added to planner's) */
+    const int32_t *sliced_cuts;
+    int32_t flags;                       /* TQC_FLAG_* */
+} tqc_plan_opts;
+
+/* Fill defaults: every qubit free, TQC_PREC_AUTO, TQC_PLANNER_AUTO, no budget. */
+TQC_API void tqc_plan_opts_default(tqc_plan_opts *opts);
+
+/*
+ * Plan the contraction (host only; no device work): contraction order
+ * (§III-E-1), slicing of the most size-reducing cut edges until inputs, then
+ * intermediates, fit the budget (§III-E-2), per-step kernel class, operand
+ * precision and tensor layouts.
+ */
+TQC_API tqc_status tqc_plan(tqc_net_t net, const tqc_plan_opts *opts, tqc_plan_t *out);
+
+/*
+ * Plan totals.  flops = 2 * multiply-adds over all steps and slices (the
+ * paper's cost unit, §III-C, counts the multiplications); bytes = algorithmic
+ * HBM bytes (operands read once, results written once); any pointer may be NULL.
+ */
+TQC_API tqc_status tqc_plan_info(tqc_plan_t plan, double *flops, double *bytes, int32_t *n_slices,
+                                 int32_t *n_steps);
+
+/*
+ * One step of a plan: log2 of the GEMM view C[M,N] = sum_K A[M,K] B[N,K]
+ * (M = left free outputs x left open cuts, N = right ones, K = shared cuts),
+ * the kernel class (0 = CUDA-core, 1 = tcgen05 tensor core) and operand type
+ * (TQC_PREC_*).  Any pointer may be NULL.
+ */
+TQC_API tqc_status tqc_plan_step(tqc_plan_t plan, int32_t step, int32_t *log2_m, int32_t *log2_n,
+                                 int32_t *log2_k, int32_t *kernel_class, int32_t *precision);
+
+/*
+ * Plan summary as JSON in buf (NUL-terminated, truncated to size).  Returns
+ * the full length needed, excluding the NUL, or -1 on a bad handle.
+ */
+TQC_API int32_t tqc_plan_describe(tqc_plan_t plan, char *buf, int32_t size);
+
+/*
+ * Reconstruct the bin into caller-owned device memory d_out (2^F elements of
+ * out_dtype, TQC_F32 or TQC_F64), stream-ordered on cuda_stream (a
+ * cudaStream_t; NULL = legacy default stream).
+ *   fixed_bits : NULL = the plan's bin; else n_qubits bytes giving new bit
+ *                values of the non-free qubits (same free set).
+ *   z_out      : NULL, or host pointer receiving the total mass Z (FP64); a
+ *                non-NULL z_out synchronises the stream.
+ * Steps: bin restriction and layout (ingest), the pairwise contractions,
+ * FP64 sum over slices, renormalisation by Z.  The first call allocates the
+ * plan's workspace.
+ */
+TQC_API tqc_status tqc_contract(tqc_plan_t plan, const uint8_t *fixed_bits, void *d_out, int32_t out_dtype,
+                                double *z_out, void *cuda_stream);
+
+/*
+ * End-to-end form with host buffers: copies every subcircuit tensor from
+ * host_tensors[j] (dtype in_dtype, NULL = unchanged) to the device, runs
+ * tqc_contract into a plan-owned device buffer, copies the 2^F results into
+ * host_out (out_dtype) and synchronises the stream.
+ */
+TQC_API tqc_status tqc_contract_host(tqc_plan_t plan, const void *const *host_tensors, int32_t in_dtype,
+                                     void *host_out, int32_t out_dtype, double *z_out, void *cuda_stream);
+
+/*
+ * Many plans (independent networks of uneven sizes) in one persistent
+ * launch.  d_outs[i] receives plan i's bin (FP32).  Plans must each have been
+ * contracted once (workspace allocated).  The launch is stream-ordered and
+ * contains no host synchronisation, so it can be captured in a CUDA graph.
+ * Device-side waits are bounded; a wait that gives up makes the call return
+ * TQC_ERR_TIMEOUT at the next synchronising call (tqc_batch_status).
+ */
+TQC_API tqc_status tqc_contract_batch(const tqc_plan_t *plans, void *const *d_outs, int32_t n,
+                                      void *cuda_stream);
+
+/*
+ * Per-step device timing (for roofline reporting).  enable = 1 makes every
+ * following tqc_contract record a CUDA event pair, on the caller's stream,
+ * around each pairwise-step launch; enable = 0 stops recording and clears
+ * the records.  tqc_plan_step_time synchronises on the recorded events and
+ * returns the mean duration (ms) and number of recorded launches of `step`.
+ */
+TQC_API tqc_status tqc_plan_profile(tqc_plan_t plan, int32_t enable);
+TQC_API tqc_status tqc_plan_step_time(tqc_plan_t plan, int32_t step, double *mean_ms, int32_t *launches);
+
+TQC_API tqc_status tqc_plan_destroy(tqc_plan_t plan);
+
+/* Thread-local description of the last error ("" if none). */
+TQC_API const char *tqc_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TQC_H_ */

@@ -1,0 +1,200 @@
+// Device helpers shared by the step kernels: bit deposit, precision
+// conversions, and the scatter epilogue that writes a staged GEMM tile into a
+// bit-permuted tensor layout.
+//
+// A tile of Me x Ne results sits in shared memory, row-major (pitch Ne + 4)
+// or column-major (pitch Me + 4).  Its elements are written in the order of
+// the destination layout: the tile-local output index t enumerates the
+// tile's result bits (tileMask) from the lowest, so runs of consecutive t are
+// runs of consecutive addresses (2^L long).  Two small tables split every
+// index computation into a low part (t & 127) and a high part (t >> 7):
+//   staging index   s(t) = s_lo[t & 127] + s_hi[t >> 7]
+//   element offset  g(t) = g_lo[t & 127] + g_hi[t >> 7]
+// (both are sums because the row and column bits occupy disjoint positions).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "tqc_internal.h"
+
+namespace tqc {
+
+// Deposit the low bits of `src` into the set bits of `mask`, lowest first.
+__device__ __forceinline__ uint64_t pdep64(uint64_t src, uint64_t mask) {
+    uint64_t r = 0;
+    while (mask) {
+        uint64_t low = mask & (~mask + 1);
+        if (src & 1) r |= low;
+        src >>= 1;
+        mask ^= low;
+    }
+    return r;
+}
+
+__device__ __forceinline__ uint32_t pdep32(uint32_t src, uint32_t mask) {
+    uint32_t r = 0;
+    while (mask) {
+        uint32_t low = mask & (~mask + 1);
+        if (src & 1) r |= low;
+        src >>= 1;
+        mask ^= low;
+    }
+    return r;
+}
+
+// Gather the bits of `x` at the set bits of `mask` into the low bits.
+__device__ __forceinline__ uint32_t pext32(uint32_t x, uint32_t mask) {
+    uint32_t r = 0, k = 0;
+    while (mask) {
+        uint32_t low = mask & (~mask + 1);
+        if (x & low) r |= 1u << k;
+        ++k;
+        mask ^= low;
+    }
+    return r;
+}
+
+// FP32 -> TF32 (round to nearest, ties away), returned as FP32 bits.
+__device__ __forceinline__ float to_tf32(float v) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
+    return __uint_as_float(r);
+}
+
+// Base element offset of the tile (rt, ct) in the result layout.
+__device__ __forceinline__ uint64_t tile_base(const EpiParams &e, uint64_t rt, uint64_t ct) {
+    return pdep64(rt, e.highR) | pdep64(ct, e.highC);
+}
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
+    __nv_bfloat162 p = __floats2bfloat162_rn(a, b);
+    return *(uint32_t *)&p;
+}
+
+// Store `vw` (1 or 4) values to consecutive elements starting at `off`.
+__device__ __forceinline__ void store_run_f32(const EpiParams &e, uint64_t off, const float *v, int vw) {
+    switch (e.mode) {
+        case EPI_F32: {
+            float *o = (float *)e.out + off;
+            if (vw == 4) *(float4 *)o = make_float4(v[0], v[1], v[2], v[3]);
+            else o[0] = v[0];
+        } break;
+        case EPI_TF32: {
+            float *o = (float *)e.out + off;
+            if (vw == 4) *(float4 *)o = make_float4(to_tf32(v[0]), to_tf32(v[1]), to_tf32(v[2]), to_tf32(v[3]));
+            else o[0] = to_tf32(v[0]);
+        } break;
+        case EPI_BF16: {
+            __nv_bfloat16 *o = (__nv_bfloat16 *)e.out + off;
+            if (vw == 4) *(uint2 *)o = make_uint2(pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]));
+            else o[0] = __float2bfloat16_rn(v[0]);
+        } break;
+        case EPI_BF16X2: {
+            __nv_bfloat16 *oh = (__nv_bfloat16 *)e.out + off;
+            __nv_bfloat16 *ol = (__nv_bfloat16 *)e.out_lo + off;
+            float h[4], l[4];
+            for (int i = 0; i < vw; ++i) {
+                __nv_bfloat16 b = __float2bfloat16_rn(v[i]);
+                h[i] = __bfloat162float(b);
+                l[i] = v[i] - h[i];
+            }
+            if (vw == 4) {
+                *(uint2 *)oh = make_uint2(pack_bf16x2(h[0], h[1]), pack_bf16x2(h[2], h[3]));
+                *(uint2 *)ol = make_uint2(pack_bf16x2(l[0], l[1]), pack_bf16x2(l[2], l[3]));
+            } else {
+                oh[0] = __float2bfloat16_rn(h[0]);
+                ol[0] = __float2bfloat16_rn(l[0]);
+            }
+        } break;
+        case EPI_F64_SET: {
+            double *o = (double *)e.out + off;
+            if (vw == 4) {
+                ((double2 *)o)[0] = make_double2(v[0], v[1]);
+                ((double2 *)o)[1] = make_double2(v[2], v[3]);
+            } else {
+                o[0] = v[0];
+            }
+        } break;
+        case EPI_F64_ADD: {
+            double *o = (double *)e.out + off;
+            if (vw == 4) {
+                double2 a = ((double2 *)o)[0], b = ((double2 *)o)[1];
+                ((double2 *)o)[0] = make_double2(a.x + v[0], a.y + v[1]);
+                ((double2 *)o)[1] = make_double2(b.x + v[2], b.y + v[3]);
+            } else {
+                o[0] += v[0];
+            }
+        } break;
+        case EPI_OUT_F32: {
+            const float s = (float)e.zinfo[1];
+            float *o = (float *)e.out + off;
+            if (vw == 4) __stcs((float4 *)o, make_float4(v[0] * s, v[1] * s, v[2] * s, v[3] * s));
+            else o[0] = v[0] * s;
+        } break;
+        case EPI_OUT_F64: {
+            const double s = e.zinfo[1];
+            double *o = (double *)e.out + off;
+            if (vw == 4) {
+                ((double2 *)o)[0] = make_double2(v[0] * s, v[1] * s);
+                ((double2 *)o)[1] = make_double2(v[2] * s, v[3] * s);
+            } else {
+                o[0] = v[0] * s;
+            }
+        } break;
+        default: break;
+    }
+}
+
+struct EpiTables {
+    uint32_t s_lo[128];
+    uint32_t s_hi[256];
+    uint64_t g_lo[128];
+    uint64_t g_hi[256];
+};
+
+// Fill the tables (tile independent) for a staging buffer of the given
+// orientation and pitch.  Threads [0, nthreads) of the caller cooperate.
+__device__ __forceinline__ void epi_tables_init(EpiTables *tb, const EpiParams &e, bool rowmajor, int pitch,
+                                                int tid, int nthreads) {
+    for (int u = tid; u < 384; u += nthreads) {
+        const bool lo = u < 128;
+        const uint32_t t = lo ? (uint32_t)u : (uint32_t)(u - 128) << 7;
+        const uint32_t i = pext32(t, e.lowRc), j = pext32(t, e.lowCc);
+        const uint32_t s = rowmajor ? i * pitch + j : j * pitch + i;
+        const uint64_t g = pdep64(t, e.tileMask);
+        if (lo) {
+            tb->s_lo[u] = s;
+            tb->g_lo[u] = g;
+        } else {
+            tb->s_hi[u - 128] = s;
+            tb->g_hi[u - 128] = g;
+        }
+    }
+}
+
+// Write the staged tile (E = 2^(a+b) elements) to its destination.
+__device__ __forceinline__ void epi_readout(const EpiTables *tb, const float *stg, const EpiParams &e,
+                                            uint64_t base, int E, int tid, int nthreads) {
+    if (e.L >= 2) {
+#pragma unroll 4
+        for (int t = tid * 4; t < E; t += nthreads * 4) {
+            const uint32_t sh = tb->s_hi[t >> 7];
+            const int tl = t & 127;
+            float v[4];
+            v[0] = stg[sh + tb->s_lo[tl]];
+            v[1] = stg[sh + tb->s_lo[tl + 1]];
+            v[2] = stg[sh + tb->s_lo[tl + 2]];
+            v[3] = stg[sh + tb->s_lo[tl + 3]];
+            store_run_f32(e, base + tb->g_hi[t >> 7] + tb->g_lo[tl], v, 4);
+        }
+    } else {
+        for (int t = tid; t < E; t += nthreads) {
+            float v = stg[tb->s_hi[t >> 7] + tb->s_lo[t & 127]];
+            store_run_f32(e, base + tb->g_hi[t >> 7] + tb->g_lo[t & 127], &v, 1);
+        }
+    }
+}
+
+}  // namespace tqc

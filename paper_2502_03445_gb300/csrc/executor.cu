@@ -1,0 +1,298 @@
+// Executor: workspace allocation and the launch sequence of a plan on the
+// caller's stream.
+//
+//   for every slice (assignment of the sliced cut edges, §III-E-2):
+//       ingest the leaves that depend on it (bin restriction + layout + cast)
+//       run the pairwise steps; the last one expands the output indices into
+//       the bin order and writes (or adds, in FP64, across slices)
+//   total mass Z of the scalar network, scale = 2^{-|E|} / Z
+//   FP64 slice sum -> output (when sliced)
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <string>
+
+#include "launch.h"
+#include "tqc_internal.h"
+
+namespace tqc {
+
+namespace {
+
+tqc_status cuda_fail(cudaError_t e, const char *what) {
+    return fail(TQC_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define TQC_CUDA(call, what)                         \
+    do {                                             \
+        cudaError_t _e = (call);                     \
+        if (_e != cudaSuccess) return cuda_fail(_e, what); \
+    } while (0)
+
+char *ws_ptr(void *base, int64_t off) { return (char *)base + off; }
+
+// Source bit positions of a node tensor [c_0]..[c_{n-1}][x]: output qubit
+// out_qubits[k] is bit k; cut axis d occupies bits n_out + 2(n_cut-1-d) (+1).
+int src_pos_qubit(const Node &nd, int q) {
+    for (size_t k = 0; k < nd.out_qubits.size(); ++k)
+        if (nd.out_qubits[k] == q) return (int)k;
+    return -1;
+}
+int src_pos_cut(const Node &nd, int c) {
+    int n = (int)nd.cut_ids.size();
+    for (int d = 0; d < n; ++d)
+        if (nd.cut_ids[d] == c) return (int)nd.out_qubits.size() + 2 * (n - 1 - d);
+    return -1;
+}
+
+// Ingest arguments of leaf j for slice `slice` (fixed output bits of the bin
+// plus sliced cut values go to src_base).
+IngestArgs leaf_args(const Plan &p, const TensorPlan &t, int j, const uint8_t *fixed, int64_t slice, bool zplan) {
+    const Node &nd = p.net->nodes[j];
+    IngestArgs g;
+    g.src = nd.d_data;
+    g.src_dtype = nd.dtype;
+    int64_t base = 0;
+    if (!zplan) {
+        std::vector<char> isfree(p.net->n_qubits, 0);
+        for (int q : p.free_qubits) isfree[q] = 1;
+        for (size_t k = 0; k < nd.out_qubits.size(); ++k) {
+            int q = nd.out_qubits[k];
+            if (!isfree[q] && fixed[q]) base += 1ll << k;
+        }
+    }
+    for (size_t i = 0; i < p.sliced.size(); ++i) {
+        int c = p.sliced[i];
+        int pos = src_pos_cut(nd, c);
+        if (pos < 0) continue;
+        int64_t v = (slice >> (2 * i)) & 3;
+        base += v << pos;
+    }
+    g.src_base = base;
+    int b = 0;
+    for (auto &md : t.layout.modes) {
+        if (md.is_cut) {
+            int pos = src_pos_cut(nd, md.id);
+            g.srcpos[b++] = (int8_t)pos;
+            g.srcpos[b++] = (int8_t)(pos + 1);
+        } else {
+            g.srcpos[b++] = (int8_t)src_pos_qubit(nd, md.id);
+        }
+    }
+    g.nbits = b;
+    // total mass: sum over every output bit (a node without outputs is a plain FP64 gather)
+    g.reduce_bits = zplan ? (int)nd.out_qubits.size() : 0;
+    if (zplan) g.storage = ST_F64;
+    return g;
+}
+
+StepArgs step_args(const Plan &p, const std::vector<TensorPlan> &T, const StepPlan &st, void *ws, TileShape tile) {
+    StepArgs a;
+    const TensorPlan &ta = T[st.a], &tb = T[st.b];
+    a.A = ws_ptr(ws, ta.offset);
+    a.B = ws_ptr(ws, tb.offset);
+    if (ta.storage == ST_BF16X2) a.A_lo = ws_ptr(ws, ta.offset + ta.plane_bytes);
+    if (tb.storage == ST_BF16X2) a.B_lo = ws_ptr(ws, tb.offset + tb.plane_bytes);
+    a.mb = st.mb;
+    a.nb = st.nb;
+    a.kb = st.kb;
+    a.epi = make_epi(st.maskR, st.maskC, st.mb, st.nb, tile);
+    (void)p;
+    return a;
+}
+
+int epi_mode_of(int storage) {
+    switch (storage) {
+        case ST_BF16: return EPI_BF16;
+        case ST_BF16X2: return EPI_BF16X2;
+        case ST_TF32: return EPI_TF32;
+        case ST_F64: return EPI_Z;
+        default: return EPI_F32;
+    }
+}
+
+tqc_status launch_step(const Plan &p, const StepPlan &st, StepArgs &a, int *d_err, cudaStream_t s) {
+    cudaError_t e;
+    if (st.klass == KC_UMMA) e = launch_umma_step(st.tile, st.prec, a, d_err, s);
+    else e = launch_simt_step(st.tile, a, s);
+    (void)p;
+    if (e != cudaSuccess) return cuda_fail(e, "step launch");
+    return TQC_OK;
+}
+
+TileShape tile_of(const StepPlan &st) { return st.klass == KC_UMMA ? umma_tile(st.tile) : simt_tile(st.tile); }
+
+}  // namespace
+
+tqc_status exec_prepare(Plan *p) {
+    if (p->ready) return TQC_OK;
+    int dev = -1;
+    TQC_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
+    if (dev != p->net->device) return fail(TQC_ERR_INVALID, "current device differs from the network's device");
+    int64_t zslots = p->n_slices();
+    if (p->ws_bytes > 0) {
+        cudaError_t e = cudaMalloc(&p->d_ws, (size_t)p->ws_bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(TQC_ERR_OOM, "workspace of " + std::to_string(p->ws_bytes) + " bytes");
+        }
+    }
+    size_t zb = (size_t)p->zws_bytes + 8 * (size_t)zslots + 256;
+    cudaError_t e = cudaMalloc(&p->d_zws, zb);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(TQC_ERR_OOM, "total-mass workspace");
+    }
+    e = cudaMalloc((void **)&p->d_zinfo, 4 * sizeof(double) + 64);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(TQC_ERR_OOM, "zinfo");
+    }
+    TQC_CUDA(cudaMemset(p->d_zinfo, 0, 4 * sizeof(double) + 64), "memset");
+    // tile choice without autotuning: big tiles for big steps
+    for (auto &st : p->steps) {
+        if (st.klass == KC_UMMA) st.tile = st.nb >= 7 ? UMMA_128x128 : UMMA_128x64;
+        else st.tile = (st.mb >= 7 && st.nb >= 7) ? SIMT_128x128 : (st.mb >= 7 && st.nb >= 6 ? SIMT_128x64 : SIMT_64x64);
+    }
+    p->ready = true;
+    return TQC_OK;
+}
+
+void exec_clear_events(Plan *p) {
+    for (auto &v : p->step_events)
+        for (auto &pr : v) {
+            cudaEventDestroy((cudaEvent_t)pr[0]);
+            cudaEventDestroy((cudaEvent_t)pr[1]);
+        }
+    p->step_events.clear();
+}
+
+tqc_status exec_step_time(Plan *p, int step, double *mean_ms, int *launches) {
+    double tot = 0;
+    int n = 0;
+    if (step < (int)p->step_events.size())
+        for (auto &pr : p->step_events[step]) {
+            TQC_CUDA(cudaEventSynchronize((cudaEvent_t)pr[1]), "event sync");
+            float ms = 0;
+            TQC_CUDA(cudaEventElapsedTime(&ms, (cudaEvent_t)pr[0], (cudaEvent_t)pr[1]), "event time");
+            tot += ms;
+            ++n;
+        }
+    if (mean_ms) *mean_ms = n ? tot / n : 0.0;
+    if (launches) *launches = n;
+    return TQC_OK;
+}
+
+void exec_release(Plan *p) {
+    exec_clear_events(p);
+    if (p->d_ws) cudaFree(p->d_ws);
+    if (p->d_zws) cudaFree(p->d_zws);
+    if (p->d_zinfo) cudaFree(p->d_zinfo);
+    p->d_ws = p->d_zws = nullptr;
+    p->d_zinfo = nullptr;
+    p->ready = false;
+}
+
+tqc_status exec_contract(Plan *p, const uint8_t *fixed_bits, void *d_out, int out_dtype, double *z_out,
+                         void *stream) {
+    tqc_status st = exec_prepare(p);
+    if (st != TQC_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    const uint8_t *fixed = fixed_bits ? fixed_bits : p->fixed_bits.data();
+    if (fixed_bits)
+        for (int q = 0; q < p->net->n_qubits; ++q)
+            if (fixed_bits[q] > 1) return fail(TQC_ERR_INVALID, "fixed_bits entries must be 0 or 1");
+    const int64_t ns = p->n_slices();
+    const int nE = p->net->n_cuts;
+    double *zslice = (double *)ws_ptr(p->d_zws, p->zws_bytes);
+
+    // ---- total mass Z (scalar network: every output summed), FP64
+    for (int64_t sl = 0; sl < ns; ++sl) {
+        for (int j = 0; j < p->m; ++j) {
+            const TensorPlan &t = p->ztensors[j];
+            IngestArgs g = leaf_args(*p, t, j, fixed, sl, true);
+            g.dst = p->m == 1 ? (void *)(zslice + sl) : (void *)ws_ptr(p->d_zws, t.offset);
+            TQC_CUDA(launch_ingest(g, (int64_t)1 << t.nbits(), s), "total-mass ingest");
+        }
+        for (size_t i = 0; i < p->zsteps.size(); ++i) {
+            const StepPlan &zs = p->zsteps[i];
+            StepArgs a = step_args(*p, p->ztensors, zs, p->d_zws, simt_f64_tile());
+            a.epi.mode = EPI_Z;
+            a.epi.out = zs.final ? (void *)(zslice + sl) : (void *)ws_ptr(p->d_zws, p->ztensors[zs.c].offset);
+            TQC_CUDA(launch_simt_step_f64(a, s), "total-mass step");
+        }
+    }
+    TQC_CUDA(launch_zfinal(zslice, (int)ns, nE, !(p->flags & TQC_FLAG_NO_RENORM), p->d_zinfo, s), "zfinal");
+
+    // ---- single subcircuit: the bin is a gather of its tensor
+    if (p->m == 1) {
+        const TensorPlan &t = p->tensors[0];
+        IngestArgs g = leaf_args(*p, t, 0, fixed, 0, false);
+        g.dst = d_out;
+        g.scaled = 1;
+        g.out_f64 = out_dtype == TQC_F64;
+        g.zinfo = p->d_zinfo;
+        TQC_CUDA(launch_ingest(g, p->out_elems(), s), "ingest");
+    } else {
+        const bool sliced = ns > 1;
+        double *acc = nullptr;
+        if (sliced) acc = out_dtype == TQC_F64 ? (double *)d_out : (double *)ws_ptr(p->d_ws, p->acc_offset);
+        int *d_err = (int *)(p->d_zinfo + 2);
+        for (int64_t sl = 0; sl < ns; ++sl) {
+            for (int j = 0; j < p->m; ++j) {
+                const TensorPlan &t = p->tensors[j];
+                if (sl > 0 && !t.slice_dep) continue;
+                IngestArgs g = leaf_args(*p, t, j, fixed, sl, false);
+                g.dst = ws_ptr(p->d_ws, t.offset);
+                if (t.storage == ST_BF16X2) g.dst_lo = ws_ptr(p->d_ws, t.offset + t.plane_bytes);
+                g.storage = t.storage;
+                TQC_CUDA(launch_ingest(g, (int64_t)1 << t.nbits(), s), "ingest");
+            }
+            for (const StepPlan &sp : p->steps) {
+                if (sl > 0 && !p->tensors[sp.c].slice_dep) continue;
+                StepArgs a = step_args(*p, p->tensors, sp, p->d_ws, tile_of(sp));
+                const TensorPlan &tc = p->tensors[sp.c];
+                a.epi.zinfo = p->d_zinfo;
+                if (sp.final) {
+                    if (sliced) {
+                        a.epi.out = acc;
+                        a.epi.mode = sl == 0 ? EPI_F64_SET : EPI_F64_ADD;
+                    } else {
+                        a.epi.out = d_out;
+                        a.epi.mode = out_dtype == TQC_F64 ? EPI_OUT_F64 : EPI_OUT_F32;
+                    }
+                } else {
+                    a.epi.out = ws_ptr(p->d_ws, tc.offset);
+                    if (tc.storage == ST_BF16X2) a.epi.out_lo = ws_ptr(p->d_ws, tc.offset + tc.plane_bytes);
+                    a.epi.mode = epi_mode_of(tc.storage);
+                }
+                size_t si = &sp - p->steps.data();
+                cudaEvent_t ev[2] = {nullptr, nullptr};
+                if (p->profile) {
+                    TQC_CUDA(cudaEventCreate(&ev[0]), "event");
+                    TQC_CUDA(cudaEventCreate(&ev[1]), "event");
+                    TQC_CUDA(cudaEventRecord(ev[0], s), "event record");
+                }
+                st = launch_step(*p, sp, a, d_err, s);
+                if (st != TQC_OK) return st;
+                if (p->profile) {
+                    TQC_CUDA(cudaEventRecord(ev[1], s), "event record");
+                    if (p->step_events.size() < p->steps.size()) p->step_events.resize(p->steps.size());
+                    p->step_events[si].push_back({(void *)ev[0], (void *)ev[1]});
+                }
+            }
+        }
+        if (sliced) TQC_CUDA(launch_finalize(acc, d_out, out_dtype == TQC_F64, p->d_zinfo, p->out_elems(), s), "finalize");
+    }
+    if (z_out) {
+        double zi[4];
+        TQC_CUDA(cudaMemcpyAsync(zi, p->d_zinfo, sizeof zi, cudaMemcpyDeviceToHost, s), "z copy");
+        TQC_CUDA(cudaStreamSynchronize(s), "sync");
+        *z_out = zi[0];
+        if (((int *)(zi + 2))[0] != 0) return fail(TQC_ERR_TIMEOUT, "a tensor-core step gave up waiting on its pipeline");
+    }
+    return TQC_OK;
+}
+
+}  // namespace tqc

@@ -1,0 +1,37 @@
+// Host-side launchers of the device kernels (one per kernel family).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "tqc_internal.h"
+
+namespace tqc {
+
+// CUDA-core step tiles (FP32), chosen by the autotuner
+enum SimtCfg { SIMT_64x64 = 0, SIMT_128x128 = 1, SIMT_128x64 = 2, SIMT_N_CFG = 3 };
+
+struct TileShape {
+    int log_bm, log_bn;
+};
+
+TileShape simt_tile(int cfg);
+TileShape simt_f64_tile();
+int sm_count();
+
+cudaError_t launch_simt_step(int cfg, const StepArgs &a, cudaStream_t s);
+cudaError_t launch_simt_step_f64(const StepArgs &a, cudaStream_t s);
+cudaError_t launch_ingest(const IngestArgs &g, int64_t n_dst, cudaStream_t s);
+cudaError_t launch_zfinal(const double *zslice, int n, int n_cuts, int renorm, double *zinfo, cudaStream_t s);
+cudaError_t launch_finalize(const double *acc, void *out, int out_f64, const double *zinfo, int64_t n,
+                            cudaStream_t s);
+
+// tcgen05 step (umma.cu)
+enum UmmaCfg { UMMA_128x128 = 0, UMMA_128x64 = 1, UMMA_N_CFG = 2 };
+TileShape umma_tile(int cfg);
+// prec: TQC_PREC_BF16 / TQC_PREC_BF16X3 / TQC_PREC_TF32
+cudaError_t launch_umma_step(int cfg, int prec, const StepArgs &a, int *d_err, cudaStream_t s);
+
+// Epilogue parameters for a step given its result masks and tile shape.
+EpiParams make_epi(uint64_t maskR, uint64_t maskC, int mb, int nb, TileShape t);
+
+}  // namespace tqc

@@ -1,0 +1,430 @@
+// tcgen05 tensor-core pairwise step for sm_103a.
+//
+// C[r, c] = sum_k A[r, k] B[c, k] over the shared cut edges of two subcircuit
+// tensors (§III-B, Fig. tensor_contraction) when K = 4^{#shared cuts} is large
+// enough for the step to be a real contraction.  Operands are K-major BF16
+// (or TF32, or a BF16 hi/lo pair for the split form) written by the producing
+// step's epilogue; the result goes through the same bit-scatter epilogue as
+// the CUDA-core step (Kronecker expansion of output indices for the last
+// step, Eq. reconstruction).
+//
+// One persistent CTA per SM, warp-specialised:
+//   warp 0      TMA producer: 128B-swizzled A and B k-blocks into a ring of
+//               shared-memory stages (mbarrier complete_tx)
+//   warp 1      allocates TMEM (two FP32 accumulators of 128 x BN) and issues
+//               tcgen05.mma from one thread; tcgen05.commit frees stages and
+//               hands accumulators to the epilogue
+//   warps 2..5  epilogue: tcgen05.ld 32 columns at a time, stage the tile in
+//               shared memory in the orientation that makes the result's
+//               lowest bits contiguous, then write 16-byte runs to HBM
+// Every wait is bounded (clock64); a wait that gives up sets an error word,
+// drains the copies and MMAs it issued, frees TMEM and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <mutex>
+
+#include "device_common.cuh"
+#include "launch.h"
+
+namespace tqc {
+
+namespace {
+
+constexpr int BM = 128;
+constexpr int EPI_WARPS = 8;
+constexpr int EPI_THREADS = 32 * EPI_WARPS;
+constexpr int NTHREADS = 64 + EPI_THREADS;
+constexpr long long WAIT_CYCLES = 4000000000ll;  // about 2 s at the boost clock
+
+enum Kind { K_BF16 = 0, K_BF16X3 = 1, K_TF32 = 2 };
+
+struct UmmaParams {
+    int64_t n_tiles;
+    int64_t col_tiles;
+    int32_t k_blocks;
+    int32_t rowmajor;  // staging orientation (1: the result's lowest bit is a column bit)
+    EpiParams epi;
+    int *err;
+};
+
+template <int BN, int KIND>
+struct Cfg {
+    static constexpr int ELEM = KIND == K_TF32 ? 4 : 2;
+    static constexpr int BK = 128 / ELEM;          // one 128-byte swizzle atom of K
+    static constexpr int PLANES = KIND == K_BF16X3 ? 2 : 1;
+    static constexpr int A_BYTES = BM * 128;
+    static constexpr int B_BYTES = BN * 128;
+    static constexpr int STAGE_BYTES = PLANES * (A_BYTES + B_BYTES);
+    static constexpr int STAGES = KIND == K_BF16X3 ? 2 : (BN == 64 ? 6 : 4);
+    static constexpr int PITCH_R = BN + 4;         // row-major staging pitch (floats)
+    static constexpr int PITCH_C = BM + 4;         // column-major staging pitch
+    static constexpr int STG_BYTES = (BM * PITCH_R > BN * PITCH_C ? BM * PITCH_R : BN * PITCH_C) * 4;
+    static constexpr int BAR_BYTES = 256;
+    static constexpr int SMEM = 1024 + STAGES * STAGE_BYTES + STG_BYTES + (int)sizeof(EpiTables) + BAR_BYTES;
+    static constexpr int TMEM_COLS = 2 * BN;
+    // instruction descriptor: D = F32, A/B = BF16 (1) or TF32 (2), K-major, N >> 3, M >> 4
+    static constexpr uint32_t IDESC = (1u << 4) | ((KIND == K_TF32 ? 2u : 1u) << 7) |
+                                      ((KIND == K_TF32 ? 2u : 1u) << 10) | ((uint32_t)(BN >> 3) << 17) |
+                                      ((uint32_t)(BM >> 4) << 24);
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait for the phase of `parity` to complete.  Returns false (and
+// raises the CTA's abort flag) when the wait gives up or another role did.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag) {
+    long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (*abort_flag) return false;
+        if (clock64() - t0 > WAIT_CYCLES) {
+            *abort_flag = 1;
+            return false;
+        }
+    }
+    return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int c0, int c1, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            smem_u32(dst)),
+        "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row atoms
+// 1024 bytes apart (stride byte offset), leading byte offset unused.
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr) {
+    uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)(1024 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+
+template <int KIND>
+__device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    if (KIND == K_TF32)
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+                d_tmem),
+            "l"(a), "l"(b), "r"(idesc), "r"(acc));
+    else
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+                d_tmem),
+            "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+
+template <int BN, int KIND>
+__global__ void __launch_bounds__(NTHREADS, 1)
+    umma_step_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tB,
+                     const __grid_constant__ CUtensorMap tAl, const __grid_constant__ CUtensorMap tBl,
+                     const UmmaParams P) {
+    using C = Cfg<BN, KIND>;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t *stages = smem;
+    float *stg = (float *)(smem + C::STAGES * C::STAGE_BYTES);
+    EpiTables *tb = (EpiTables *)(smem + C::STAGES * C::STAGE_BYTES + C::STG_BYTES);
+    uint64_t *full = (uint64_t *)(smem + C::STAGES * C::STAGE_BYTES + C::STG_BYTES + sizeof(EpiTables));
+    uint64_t *empty = full + C::STAGES;
+    uint64_t *tfull = empty + C::STAGES;
+    uint64_t *tempty = tfull + 2;
+    uint64_t *drain = tempty + 2;
+    uint32_t *tmem_slot = (uint32_t *)(drain + 1);
+    volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < C::STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(&tfull[a], 1);
+            mbar_init(&tempty[a], EPI_WARPS);
+        }
+        mbar_init(drain, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"((uint32_t)C::TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+    const EpiParams &e = P.epi;
+
+    if (warp == 0) {
+        // ------------------------------------------------ TMA producer
+        if (lane == 0) {
+            asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tA) : "memory");
+            asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tB) : "memory");
+            int64_t it = 0;
+            bool ok = true;
+            for (int64_t tile = blockIdx.x; ok && tile < P.n_tiles; tile += gridDim.x) {
+                const int rt = (int)(tile / P.col_tiles), ct = (int)(tile - (int64_t)rt * P.col_tiles);
+                for (int kb = 0; kb < P.k_blocks; ++kb, ++it) {
+                    const int s = (int)(it % C::STAGES);
+                    const uint32_t ph = (uint32_t)((it / C::STAGES) & 1);
+                    if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    uint8_t *sa = stages + s * C::STAGE_BYTES;
+                    mbar_expect_tx(&full[s], C::STAGE_BYTES);
+                    tma_load_2d(sa, &tA, kb * C::BK, rt * BM, &full[s]);
+                    tma_load_2d(sa + C::A_BYTES, &tB, kb * C::BK, ct * BN, &full[s]);
+                    if (KIND == K_BF16X3) {
+                        tma_load_2d(sa + C::A_BYTES + C::B_BYTES, &tAl, kb * C::BK, rt * BM, &full[s]);
+                        tma_load_2d(sa + 2 * C::A_BYTES + C::B_BYTES, &tBl, kb * C::BK, ct * BN, &full[s]);
+                    }
+                }
+            }
+            if (!ok) {
+                // drain: wait (bounded) for the copies still in flight in every stage
+                for (int64_t j = it > C::STAGES ? it - C::STAGES : 0; j < it; ++j) {
+                    long long t0 = clock64();
+                    while (!mbar_try_wait(&full[j % C::STAGES], (uint32_t)((j / C::STAGES) & 1)) &&
+                           clock64() - t0 < WAIT_CYCLES) {
+                    }
+                }
+            }
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            int64_t it = 0, lt = 0;
+            bool ok = true;
+            for (int64_t tile = blockIdx.x; ok && tile < P.n_tiles; tile += gridDim.x, ++lt) {
+                const int acc = (int)(lt & 1);
+                const uint32_t aph = (uint32_t)((lt >> 1) & 1);
+                if (!mbar_wait(&tempty[acc], aph ^ 1u, abort_flag)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t d = tmem_base + (uint32_t)(acc * BN);
+                for (int kb = 0; kb < P.k_blocks; ++kb, ++it) {
+                    const int s = (int)(it % C::STAGES);
+                    const uint32_t ph = (uint32_t)((it / C::STAGES) & 1);
+                    if (!mbar_wait(&full[s], ph, abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t a0 = smem_u32(stages + s * C::STAGE_BYTES);
+                    const uint32_t b0 = a0 + C::A_BYTES;
+                    const uint32_t al = b0 + C::B_BYTES;
+                    const uint32_t bl = al + C::A_BYTES;
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {  // four 32-byte K slices of the 128-byte atom
+                        const uint64_t da = umma_desc(a0 + 32 * k), db = umma_desc(b0 + 32 * k);
+                        umma<KIND>(d, da, db, C::IDESC, (kb | k) != 0);
+                        if (KIND == K_BF16X3) {
+                            umma<KIND>(d, da, umma_desc(bl + 32 * k), C::IDESC, 1u);
+                            umma<KIND>(d, umma_desc(al + 32 * k), db, C::IDESC, 1u);
+                        }
+                    }
+                    umma_commit(&empty[s]);
+                }
+                if (ok) umma_commit(&tfull[acc]);
+            }
+            // every MMA issued so far has completed once this commit arrives
+            umma_commit(drain);
+            long long t0 = clock64();
+            while (!mbar_try_wait(drain, 0) && clock64() - t0 < WAIT_CYCLES) {
+            }
+        }
+    } else {
+        // ------------------------------------------------ epilogue
+        // two warpgroups: each reads all 128 TMEM lanes for half of the columns
+        const int lane_grp = warp & 3;          // TMEM lanes this warp may read
+        const int half = (warp - 2) >> 2;       // column half of this warpgroup
+        const int row = lane_grp * 32 + lane;   // accumulator row
+        const int etid = threadIdx.x - 64;      // 0..255
+        const int Me = 1 << e.a_bits, Ne = 1 << e.b_bits;
+        const int E = Me * Ne;
+        epi_tables_init(tb, e, P.rowmajor != 0, P.rowmajor ? C::PITCH_R : C::PITCH_C, etid, EPI_THREADS);
+        asm volatile("bar.sync 1, %0;" ::"n"(EPI_THREADS) : "memory");
+        int64_t lt = 0;
+        for (int64_t tile = blockIdx.x; tile < P.n_tiles; tile += gridDim.x, ++lt) {
+            const int acc = (int)(lt & 1);
+            const uint32_t aph = (uint32_t)((lt >> 1) & 1);
+            mbar_wait(&tfull[acc], aph, abort_flag);
+            asm volatile("bar.sync 1, %0;" ::"n"(EPI_THREADS) : "memory");
+            if (*abort_flag) break;
+            tc_fence_after();
+            const uint32_t tbase = tmem_base + ((uint32_t)(lane_grp * 32) << 16) + (uint32_t)(acc * BN);
+#pragma unroll 1
+            for (int ch = half * (BN / 64); ch < (half + 1) * (BN / 64); ++ch) {
+                uint32_t r[32];
+                tmem_ld32(tbase + ch * 32, r);
+                if (row < Me) {
+                    if (P.rowmajor) {
+                        float *dst = stg + row * C::PITCH_R + ch * 32;
+#pragma unroll
+                        for (int j = 0; j < 32; j += 4)
+                            if (ch * 32 + j < Ne)
+                                *(float4 *)(dst + j) = make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]),
+                                                                   __uint_as_float(r[j + 2]), __uint_as_float(r[j + 3]));
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 32; ++j)
+                            if (ch * 32 + j < Ne) stg[(ch * 32 + j) * C::PITCH_C + row] = __uint_as_float(r[j]);
+                    }
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tempty[acc]);
+            asm volatile("bar.sync 1, %0;" ::"n"(EPI_THREADS) : "memory");
+            const int64_t rt = tile / P.col_tiles;
+            const int64_t ct = tile - rt * P.col_tiles;
+            epi_readout(tb, stg, e, tile_base(e, (uint64_t)rt, (uint64_t)ct), E, etid, EPI_THREADS);
+            asm volatile("bar.sync 1, %0;" ::"n"(EPI_THREADS) : "memory");
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && *abort_flag && P.err) atomicExch(P.err, 1);
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+                     "r"((uint32_t)C::TMEM_COLS)
+                     : "memory");
+    }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+std::once_flag g_encode_once;
+
+cudaError_t get_encode() {
+    std::call_once(g_encode_once, [] {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            g_encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+    });
+    return g_encode ? cudaSuccess : cudaErrorNotSupported;
+}
+
+// 2-D K-major operand: `rows` rows of `k` elements, box = (BK elements, box_rows)
+cudaError_t encode(CUtensorMap *m, const void *ptr, int elem, uint64_t k, uint64_t rows, uint32_t bk,
+                   uint32_t box_rows) {
+    if (!ptr || ((uintptr_t)ptr & 15) || rows > (1ull << 32)) return cudaErrorInvalidValue;
+    cuuint64_t dims[2] = {k, rows};
+    cuuint64_t strides[1] = {k * (uint64_t)elem};
+    cuuint32_t box[2] = {bk, box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = g_encode(m, elem == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                          const_cast<void *>(ptr), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                          CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+template <int BN, int KIND>
+cudaError_t launch_kind(const StepArgs &a, int *d_err, cudaStream_t s) {
+    using C = Cfg<BN, KIND>;
+    cudaError_t e = get_encode();
+    if (e != cudaSuccess) return e;
+    static bool attr = false;
+    if (!attr) {
+        e = cudaFuncSetAttribute(umma_step_kernel<BN, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    const uint64_t M = 1ull << a.mb, N = 1ull << a.nb, K = 1ull << a.kb;
+    if (K < (uint64_t)C::BK) return cudaErrorInvalidValue;
+    CUtensorMap tA, tB, tAl, tBl;
+    if ((e = encode(&tA, a.A, C::ELEM, K, M, C::BK, BM)) != cudaSuccess) return e;
+    if ((e = encode(&tB, a.B, C::ELEM, K, N, C::BK, BN)) != cudaSuccess) return e;
+    if (KIND == K_BF16X3) {
+        if ((e = encode(&tAl, a.A_lo, C::ELEM, K, M, C::BK, BM)) != cudaSuccess) return e;
+        if ((e = encode(&tBl, a.B_lo, C::ELEM, K, N, C::BK, BN)) != cudaSuccess) return e;
+    } else {
+        tAl = tA;
+        tBl = tB;
+    }
+    UmmaParams p;
+    p.epi = a.epi;
+    const int64_t row_tiles = (int64_t)1 << (a.mb - a.epi.a_bits);
+    p.col_tiles = (int64_t)1 << (a.nb - a.epi.b_bits);
+    p.n_tiles = row_tiles * p.col_tiles;
+    p.k_blocks = (int)(K / C::BK);
+    p.rowmajor = (a.epi.lowCc & 1u) ? 1 : 0;
+    p.err = d_err;
+    const int64_t grid = std::min<int64_t>(p.n_tiles, sm_count());
+    umma_step_kernel<BN, KIND><<<(unsigned)grid, NTHREADS, C::SMEM, s>>>(tA, tB, tAl, tBl, p);
+    return cudaGetLastError();
+}
+
+template <int BN>
+cudaError_t launch_bn(int prec, const StepArgs &a, int *d_err, cudaStream_t s) {
+    switch (prec) {
+        case TQC_PREC_BF16: return launch_kind<BN, K_BF16>(a, d_err, s);
+        case TQC_PREC_BF16X3: return launch_kind<BN, K_BF16X3>(a, d_err, s);
+        case TQC_PREC_TF32: return launch_kind<BN, K_TF32>(a, d_err, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace
+
+TileShape umma_tile(int cfg) { return cfg == UMMA_128x64 ? TileShape{7, 6} : TileShape{7, 7}; }
+
+cudaError_t launch_umma_step(int cfg, int prec, const StepArgs &a, int *d_err, cudaStream_t s) {
+    if (cfg == UMMA_128x64) return launch_bn<64>(prec, a, d_err, s);
+    return launch_bn<128>(prec, a, d_err, s);
+}
+
+}  // namespace tqc

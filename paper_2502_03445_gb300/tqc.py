@@ -1,0 +1,283 @@
+"""Thin ctypes binding of libtqc (argument marshalling only).
+
+Every step of the reconstruction runs in the library's CUDA kernels; this
+module only converts Python objects to the C ABI declared in
+``include/tqc.h``.  There is no Python or CPU fallback: if the library is
+missing, importing :func:`lib` raises.
+
+Device memory and streams come from PyTorch (``torch.Tensor.data_ptr()``,
+``torch.cuda.current_stream().cuda_stream``)."""
+from __future__ import annotations
+
+import ctypes
+import json
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libtqc.so")
+
+OK, ERR_INVALID, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_UNSUPPORTED = range(6)
+F64, F32 = 0, 1
+PREC_FP32, PREC_TF32, PREC_BF16, PREC_BF16X3, PREC_AUTO = range(5)
+PLANNER_GREEDY, PLANNER_EXHAUSTIVE, PLANNER_LEARNED, PLANNER_AUTO = range(4)
+FLAG_NO_RENORM = 1
+PREC_NAMES = {"fp32": PREC_FP32, "tf32": PREC_TF32, "bf16": PREC_BF16, "bf16x3": PREC_BF16X3, "auto": PREC_AUTO}
+
+# every symbol include/tqc.h declares
+EXPORTS = ["tqc_network_create", "tqc_network_upload", "tqc_destroy", "tqc_plan_opts_default", "tqc_plan",
+           "tqc_plan_info", "tqc_plan_step", "tqc_plan_describe", "tqc_contract", "tqc_contract_host",
+           "tqc_contract_batch", "tqc_plan_profile", "tqc_plan_step_time", "tqc_plan_destroy", "tqc_last_error"]
+
+
+class TqcError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"tqc status {status}: {msg}")
+        self.status = status
+
+
+class Subcircuit(ctypes.Structure):
+    _fields_ = [("n_out", ctypes.c_int32), ("out_qubits", ctypes.c_void_p),
+                ("n_cut", ctypes.c_int32), ("cut_ids", ctypes.c_void_p),
+                ("cut_role", ctypes.c_void_p), ("dtype", ctypes.c_int32), ("data", ctypes.c_void_p)]
+
+
+class PlanOpts(ctypes.Structure):
+    _fields_ = [("use_free_mask", ctypes.c_int32), ("free_mask_lo", ctypes.c_uint64),
+                ("free_mask_hi", ctypes.c_uint64), ("fixed_bits", ctypes.c_void_p),
+                ("precision", ctypes.c_int32), ("planner", ctypes.c_int32),
+                ("mem_budget_bytes", ctypes.c_uint64), ("costmodel_path", ctypes.c_char_p),
+                ("autotune", ctypes.c_int32), ("n_order", ctypes.c_int32), ("order", ctypes.c_void_p),
+                ("n_sliced", ctypes.c_int32), ("sliced_cuts", ctypes.c_void_p), ("flags", ctypes.c_int32)]
+
+
+_lib = None
+
+
+def lib():
+    """Load libtqc.so (built by ``__graft_entry__.build()``); raises if absent."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libtqc.so is not built ({LIB_PATH}); run __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i32, u8p = ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p
+        L.tqc_network_create.argtypes = [i32, i32, vp, ctypes.POINTER(vp)]
+        L.tqc_network_upload.argtypes = [vp, i32, i32, vp, vp]
+        L.tqc_destroy.argtypes = [vp]
+        L.tqc_plan_opts_default.argtypes = [ctypes.POINTER(PlanOpts)]
+        L.tqc_plan_opts_default.restype = None
+        L.tqc_plan.argtypes = [vp, ctypes.POINTER(PlanOpts), ctypes.POINTER(vp)]
+        L.tqc_plan_info.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                    ctypes.POINTER(i32), ctypes.POINTER(i32)]
+        L.tqc_plan_step.argtypes = [vp, i32] + [ctypes.POINTER(i32)] * 5
+        L.tqc_plan_describe.argtypes = [vp, ctypes.c_char_p, i32]
+        L.tqc_plan_describe.restype = i32
+        L.tqc_contract.argtypes = [vp, u8p, vp, i32, ctypes.POINTER(ctypes.c_double), vp]
+        L.tqc_contract_host.argtypes = [vp, vp, i32, vp, i32, ctypes.POINTER(ctypes.c_double), vp]
+        L.tqc_contract_batch.argtypes = [vp, vp, i32, vp]
+        L.tqc_plan_destroy.argtypes = [vp]
+        L.tqc_plan_profile.argtypes = [vp, i32]
+        L.tqc_plan_step_time.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i32)]
+        L.tqc_last_error.restype = ctypes.c_char_p
+        for name in ["tqc_network_create", "tqc_network_upload", "tqc_destroy", "tqc_plan", "tqc_plan_info",
+                     "tqc_plan_step", "tqc_contract", "tqc_contract_host", "tqc_contract_batch",
+                     "tqc_plan_destroy", "tqc_plan_profile", "tqc_plan_step_time"]:
+            getattr(L, name).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _check(st):
+    if st != OK:
+        raise TqcError(st, lib().tqc_last_error().decode())
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+class Network:
+    """A network handle.  ``net`` is any object with ``n_qubits`` and
+    ``nodes`` (each with ``out_qubits``, ``cut_ids``, ``cut_role`` and a
+    float64/float32 ``data`` array in the row-major [c_0]..[x] layout)."""
+
+    def __init__(self, net, dtype=F64, shape_only=False):
+        L = lib()
+        self.n_qubits = net.n_qubits
+        self.m = len(net.nodes)
+        self._keep = []
+        subs = (Subcircuit * self.m)()
+        npdt = np.float64 if dtype == F64 else np.float32
+        for j, nd in enumerate(net.nodes):
+            oq = np.ascontiguousarray(nd.out_qubits, dtype=np.int32)
+            ci = np.ascontiguousarray(nd.cut_ids, dtype=np.int32)
+            cr = np.ascontiguousarray(nd.cut_role, dtype=np.int8)
+            data = None if shape_only else np.ascontiguousarray(nd.data, dtype=npdt)
+            self._keep += [oq, ci, cr, data]
+            subs[j] = Subcircuit(len(oq), oq.ctypes.data if len(oq) else None, len(ci),
+                                 ci.ctypes.data if len(ci) else None, cr.ctypes.data if len(cr) else None,
+                                 dtype, None if data is None else data.ctypes.data)
+        h = ctypes.c_void_p()
+        _check(L.tqc_network_create(self.n_qubits, self.m, ctypes.cast(subs, ctypes.c_void_p), ctypes.byref(h)))
+        self._keep = None
+        self.handle = h
+        self.dtype = dtype
+        self.plans = []
+
+    def upload(self, sub, host_array, stream=None):
+        arr = np.ascontiguousarray(host_array)
+        _check(lib().tqc_network_upload(self.handle, sub, self.dtype, arr.ctypes.data, _stream_ptr(stream)))
+
+    def close(self):
+        if self.handle:
+            for p in list(self.plans):
+                p.close()
+            _check(lib().tqc_destroy(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Plan:
+    def __init__(self, net: Network, precision=PREC_AUTO, planner=PLANNER_AUTO, free_qubits=None,
+                 fixed_bits=None, mem_budget=0, order=None, sliced=None, flags=0, autotune=0,
+                 costmodel_path=None):
+        L = lib()
+        o = PlanOpts()
+        L.tqc_plan_opts_default(ctypes.byref(o))
+        if isinstance(precision, str):
+            precision = PREC_NAMES[precision]
+        o.precision = precision
+        o.planner = planner
+        keep = []
+        if free_qubits is not None:
+            o.use_free_mask = 1
+            lo = hi = 0
+            for q in free_qubits:
+                if q < 64:
+                    lo |= 1 << q
+                else:
+                    hi |= 1 << (q - 64)
+            o.free_mask_lo, o.free_mask_hi = lo, hi
+            self.free_qubits = sorted(free_qubits)
+        else:
+            self.free_qubits = list(range(net.n_qubits))
+        if fixed_bits is not None:
+            fb = np.ascontiguousarray(fixed_bits, dtype=np.uint8)
+            keep.append(fb)
+            o.fixed_bits = fb.ctypes.data
+        o.mem_budget_bytes = int(mem_budget)
+        if order is not None:
+            od = np.ascontiguousarray(np.array(order, dtype=np.int32).reshape(-1))
+            keep.append(od)
+            o.n_order = len(od) // 2
+            o.order = od.ctypes.data
+        if sliced:
+            sc = np.ascontiguousarray(sliced, dtype=np.int32)
+            keep.append(sc)
+            o.n_sliced = len(sc)
+            o.sliced_cuts = sc.ctypes.data
+        if costmodel_path:
+            o.costmodel_path = costmodel_path.encode()
+        o.flags = flags
+        o.autotune = autotune
+        h = ctypes.c_void_p()
+        _check(L.tqc_plan(net.handle, ctypes.byref(o), ctypes.byref(h)))
+        self.handle = h
+        self.net = net
+        self.n_qubits = net.n_qubits
+        net.plans.append(self)
+
+    @property
+    def out_elems(self):
+        return 1 << len(self.free_qubits)
+
+    def info(self):
+        f, b = ctypes.c_double(), ctypes.c_double()
+        ns, nst = ctypes.c_int32(), ctypes.c_int32()
+        _check(lib().tqc_plan_info(self.handle, ctypes.byref(f), ctypes.byref(b), ctypes.byref(ns),
+                                   ctypes.byref(nst)))
+        return {"flops": f.value, "bytes": b.value, "n_slices": ns.value, "n_steps": nst.value}
+
+    def step(self, i):
+        vals = [ctypes.c_int32() for _ in range(5)]
+        _check(lib().tqc_plan_step(self.handle, i, *[ctypes.byref(v) for v in vals]))
+        return dict(zip(["log2_m", "log2_n", "log2_k", "klass", "precision"], [v.value for v in vals]))
+
+    def describe(self):
+        n = lib().tqc_plan_describe(self.handle, None, 0)
+        buf = ctypes.create_string_buffer(n + 1)
+        lib().tqc_plan_describe(self.handle, buf, n + 1)
+        return json.loads(buf.value.decode())
+
+    def contract(self, out, fixed_bits=None, want_z=False, stream=None):
+        """Reconstruct into ``out`` (a CUDA torch tensor of float32/float64
+        with ``out_elems`` elements).  Returns Z when ``want_z``."""
+        import torch
+        assert out.is_cuda and out.is_contiguous() and out.numel() == self.out_elems
+        dt = F64 if out.dtype == torch.float64 else F32
+        if out.dtype not in (torch.float32, torch.float64):
+            raise TypeError("out must be float32 or float64")
+        fb = None
+        if fixed_bits is not None:
+            fb = np.ascontiguousarray(fixed_bits, dtype=np.uint8)
+        z = ctypes.c_double()
+        _check(lib().tqc_contract(self.handle, None if fb is None else fb.ctypes.data, out.data_ptr(), dt,
+                                  ctypes.byref(z) if want_z else None, _stream_ptr(stream)))
+        return z.value if want_z else None
+
+    def contract_host(self, host_tensors, host_out, in_dtype=F64, stream=None):
+        """End-to-end: host tensors in (None = unchanged), host results out."""
+        arr = (ctypes.c_void_p * self.net.m)()
+        keep = []
+        for j, t in enumerate(host_tensors or [None] * self.net.m):
+            if t is not None:
+                keep.append(t)
+                arr[j] = t.ctypes.data if isinstance(t, np.ndarray) else t.data_ptr()
+        dt = F64 if host_out.dtype in (np.float64,) or str(host_out.dtype) == "torch.float64" else F32
+        optr = host_out.ctypes.data if isinstance(host_out, np.ndarray) else host_out.data_ptr()
+        z = ctypes.c_double()
+        _check(lib().tqc_contract_host(self.handle, ctypes.cast(arr, ctypes.c_void_p) if host_tensors else None,
+                                       in_dtype, optr, dt, ctypes.byref(z), _stream_ptr(stream)))
+        return z.value
+
+    def profile(self, enable=True):
+        _check(lib().tqc_plan_profile(self.handle, int(enable)))
+
+    def step_time(self, i):
+        """(mean ms, launches) of step i over the profiled contracts."""
+        ms, n = ctypes.c_double(), ctypes.c_int32()
+        _check(lib().tqc_plan_step_time(self.handle, i, ctypes.byref(ms), ctypes.byref(n)))
+        return ms.value, n.value
+
+    def close(self):
+        if self.handle:
+            _check(lib().tqc_plan_destroy(self.handle))
+            self.handle = None
+            if self in self.net.plans:
+                self.net.plans.remove(self)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def contract_batch(plans, outs, stream=None):
+    n = len(plans)
+    hp = (ctypes.c_void_p * n)(*[p.handle.value for p in plans])
+    ho = (ctypes.c_void_p * n)(*[o.data_ptr() for o in outs])
+    _check(lib().tqc_contract_batch(ctypes.cast(hp, ctypes.c_void_p), ctypes.cast(ho, ctypes.c_void_p), n,
+                                    _stream_ptr(stream)))
