@@ -224,6 +224,34 @@ TQC_API tqc_status tqc_plan_step_time(tqc_plan_t plan, int32_t step, double *mea
 
 TQC_API tqc_status tqc_plan_destroy(tqc_plan_t plan);
 
+/*
+ * Allocation-free reconstruction.  The paper has no counterpart: this entry
+ * point exists for callers that must not allocate device memory when they
+ * reconstruct -- a process whose device memory is owned by another
+ * framework's caching allocator or capped (MPS), a latency-critical loop in
+ * which cudaMalloc/cudaFree would synchronise the device, or code whose
+ * policy forbids touching the allocator.
+ *
+ * Same result as tqc_contract for the same plan and tensors, but every
+ * intermediate lives in one file-scope device array of
+ * tqc_noalloc_scratch_bytes() bytes (16 MiB), which every GPU that loads the
+ * library holds until the process exits.  The call allocates nothing.
+ *   plan      : from tqc_plan; its network may be shape-only (data == NULL)
+ *   d_tensors : m device pointers, caller-owned, subcircuit j in the layout of
+ *               tqc_subcircuit.data, element type in_dtype (TQC_F64/TQC_F32)
+ *   fixed_bits: as in tqc_contract (NULL = the plan's bin)
+ *   d_out     : caller-owned device buffer of 2^F elements of out_dtype
+ * Returns TQC_ERR_UNSUPPORTED, before any device work, when the plan needs
+ * more scratch than the array holds.  All calls share the array: calls that
+ * overlap on the GPU (other streams, other threads) race and corrupt each
+ * other.  The first call on a device looks the array's address up with
+ * cudaGetSymbolAddress; make that first call before any stream capture.
+ */
+TQC_API tqc_status tqc_contract_noalloc(tqc_plan_t plan, const void *const *d_tensors, int32_t in_dtype,
+                                        const uint8_t *fixed_bits, void *d_out, int32_t out_dtype,
+                                        void *cuda_stream);
+TQC_API int64_t tqc_noalloc_scratch_bytes(void);
+
 /* Thread-local description of the last error ("" if none). */
 TQC_API const char *tqc_last_error(void);
 

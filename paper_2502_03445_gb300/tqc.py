@@ -28,7 +28,8 @@ PREC_NAMES = {"fp32": PREC_FP32, "tf32": PREC_TF32, "bf16": PREC_BF16, "bf16x3":
 # every symbol include/tqc.h declares
 EXPORTS = ["tqc_network_create", "tqc_network_upload", "tqc_destroy", "tqc_plan_opts_default", "tqc_plan",
            "tqc_plan_info", "tqc_plan_step", "tqc_plan_describe", "tqc_contract", "tqc_contract_host",
-           "tqc_contract_batch", "tqc_plan_profile", "tqc_plan_step_time", "tqc_plan_destroy", "tqc_last_error"]
+           "tqc_contract_batch", "tqc_plan_profile", "tqc_plan_step_time", "tqc_plan_destroy", "tqc_last_error",
+           "tqc_contract_noalloc", "tqc_noalloc_scratch_bytes"]
 
 
 class TqcError(RuntimeError):
@@ -81,6 +82,10 @@ def lib():
         L.tqc_plan_profile.argtypes = [vp, i32]
         L.tqc_plan_step_time.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i32)]
         L.tqc_last_error.restype = ctypes.c_char_p
+        L.tqc_contract_noalloc.argtypes = [vp, vp, i32, u8p, vp, i32, vp]
+        L.tqc_contract_noalloc.restype = ctypes.c_int
+        L.tqc_noalloc_scratch_bytes.argtypes = []
+        L.tqc_noalloc_scratch_bytes.restype = ctypes.c_int64
         for name in ["tqc_network_create", "tqc_network_upload", "tqc_destroy", "tqc_plan", "tqc_plan_info",
                      "tqc_plan_step", "tqc_contract", "tqc_contract_host", "tqc_contract_batch",
                      "tqc_plan_destroy", "tqc_plan_profile", "tqc_plan_step_time"]:
@@ -251,6 +256,18 @@ class Plan:
         _check(lib().tqc_contract_host(self.handle, ctypes.cast(arr, ctypes.c_void_p) if host_tensors else None,
                                        in_dtype, optr, dt, ctypes.byref(z), _stream_ptr(stream)))
         return z.value
+
+    def contract_noalloc(self, d_tensors, out, in_dtype=F64, fixed_bits=None, stream=None):
+        """Allocation-free form: ``d_tensors`` are the caller's device tensors
+        (one per subcircuit), every intermediate lives in the library's fixed
+        scratch array (see tqc_contract_noalloc in include/tqc.h)."""
+        ptrs = (ctypes.c_void_p * len(d_tensors))(*[t.data_ptr() for t in d_tensors])
+        fb = None if fixed_bits is None else np.ascontiguousarray(fixed_bits, dtype=np.uint8)
+        import torch
+        dt = F64 if out.dtype == torch.float64 else F32
+        _check(lib().tqc_contract_noalloc(self.handle, ctypes.cast(ptrs, ctypes.c_void_p), in_dtype,
+                                          None if fb is None else fb.ctypes.data, out.data_ptr(), dt,
+                                          _stream_ptr(stream)))
 
     def profile(self, enable=True):
         _check(lib().tqc_plan_profile(self.handle, int(enable)))
