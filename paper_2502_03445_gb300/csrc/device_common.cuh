@@ -73,8 +73,11 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
     return *(uint32_t *)&p;
 }
 
-// Store `vw` (1 or 4) values to consecutive elements starting at `off`.
-__device__ __forceinline__ void store_run_f32(const EpiParams &e, uint64_t off, const float *v, int vw) {
+// Store `vw` (1 or 4) values to consecutive elements starting at `off`;
+// `s` is the output scale zinfo[1] for the EPI_OUT_* modes (read once per
+// tile by the caller).
+__device__ __forceinline__ void store_run_f32(const EpiParams &e, uint64_t off, const float *v, int vw,
+                                              double s = 1.0) {
     switch (e.mode) {
         case EPI_F32: {
             float *o = (float *)e.out + off;
@@ -128,13 +131,12 @@ __device__ __forceinline__ void store_run_f32(const EpiParams &e, uint64_t off, 
             }
         } break;
         case EPI_OUT_F32: {
-            const float s = (float)e.zinfo[1];
+            const float sf = (float)s;
             float *o = (float *)e.out + off;
-            if (vw == 4) __stcs((float4 *)o, make_float4(v[0] * s, v[1] * s, v[2] * s, v[3] * s));
-            else o[0] = v[0] * s;
+            if (vw == 4) *(float4 *)o = make_float4(v[0] * sf, v[1] * sf, v[2] * sf, v[3] * sf);
+            else o[0] = v[0] * sf;
         } break;
         case EPI_OUT_F64: {
-            const double s = e.zinfo[1];
             double *o = (double *)e.out + off;
             if (vw == 4) {
                 ((double2 *)o)[0] = make_double2(v[0] * s, v[1] * s);
@@ -174,25 +176,79 @@ __device__ __forceinline__ void epi_tables_init(EpiTables *tb, const EpiParams &
     }
 }
 
+// How a thread's four consecutive output elements t..t+3 sit in the staging
+// buffer: which of t's two lowest bits run along its contiguous dimension.
+enum GatherMode { G_VEC4 = 0, G_PAIR01 = 1, G_PAIR02 = 2, G_SCALAR = 3 };
+
+struct StagePick {
+    int rowmajor;  // 1: staging [row][col] (columns contiguous), 0: [col][row]
+    int gmode;
+};
+
+// Choose the staging orientation so that the bits that vary across the
+// lanes of a warp (t bits 2..6) and the thread's own low bits fall on the
+// contiguous dimension as far as possible: conflict-free, vectorised
+// gathers.  `lowRc` / `lowCc` mark the row / column bits of t.
+__host__ __device__ inline int gather_mode(uint32_t contig) {
+    const bool b0 = contig & 1u, b1 = contig & 2u;
+    return (b0 && b1) ? G_VEC4 : b0 ? G_PAIR01 : b1 ? G_PAIR02 : G_SCALAR;
+}
+
+__host__ __device__ inline StagePick pick_staging(uint32_t lowRc, uint32_t lowCc) {
+    StagePick p;
+    int rows = 0, cols = 0;
+    for (int k = 0; k < 7; ++k) {
+        rows += (lowRc >> k) & 1u;
+        cols += (lowCc >> k) & 1u;
+    }
+    p.rowmajor = cols >= rows ? 1 : 0;
+    p.gmode = gather_mode(p.rowmajor ? lowCc : lowRc);
+    return p;
+}
+
 // Write the staged tile (E = 2^(a+b) elements) to its destination.
 __device__ __forceinline__ void epi_readout(const EpiTables *tb, const float *stg, const EpiParams &e,
-                                            uint64_t base, int E, int tid, int nthreads) {
+                                            uint64_t base, int E, int tid, int nthreads, int gmode) {
+    const double s = (e.mode == EPI_OUT_F32 || e.mode == EPI_OUT_F64) ? e.zinfo[1] : 1.0;
     if (e.L >= 2) {
 #pragma unroll 4
         for (int t = tid * 4; t < E; t += nthreads * 4) {
             const uint32_t sh = tb->s_hi[t >> 7];
             const int tl = t & 127;
+            const uint32_t s0 = sh + tb->s_lo[tl];
             float v[4];
-            v[0] = stg[sh + tb->s_lo[tl]];
-            v[1] = stg[sh + tb->s_lo[tl + 1]];
-            v[2] = stg[sh + tb->s_lo[tl + 2]];
-            v[3] = stg[sh + tb->s_lo[tl + 3]];
-            store_run_f32(e, base + tb->g_hi[t >> 7] + tb->g_lo[tl], v, 4);
+            if (gmode == G_VEC4) {
+                const float4 q = *(const float4 *)(stg + s0);
+                v[0] = q.x;
+                v[1] = q.y;
+                v[2] = q.z;
+                v[3] = q.w;
+            } else if (gmode == G_PAIR01) {
+                const float2 a = *(const float2 *)(stg + s0);
+                const float2 b = *(const float2 *)(stg + sh + tb->s_lo[tl + 2]);
+                v[0] = a.x;
+                v[1] = a.y;
+                v[2] = b.x;
+                v[3] = b.y;
+            } else if (gmode == G_PAIR02) {
+                const float2 a = *(const float2 *)(stg + s0);
+                const float2 b = *(const float2 *)(stg + sh + tb->s_lo[tl + 1]);
+                v[0] = a.x;
+                v[1] = b.x;
+                v[2] = a.y;
+                v[3] = b.y;
+            } else {
+                v[0] = stg[s0];
+                v[1] = stg[sh + tb->s_lo[tl + 1]];
+                v[2] = stg[sh + tb->s_lo[tl + 2]];
+                v[3] = stg[sh + tb->s_lo[tl + 3]];
+            }
+            store_run_f32(e, base + tb->g_hi[t >> 7] + tb->g_lo[tl], v, 4, s);
         }
     } else {
         for (int t = tid; t < E; t += nthreads) {
             float v = stg[tb->s_hi[t >> 7] + tb->s_lo[t & 127]];
-            store_run_f32(e, base + tb->g_hi[t >> 7] + tb->g_lo[t & 127], &v, 1);
+            store_run_f32(e, base + tb->g_hi[t >> 7] + tb->g_lo[t & 127], &v, 1, s);
         }
     }
 }

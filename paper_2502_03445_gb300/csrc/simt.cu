@@ -86,7 +86,7 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
                 *(float4 *)&stg[(ty * TM + u) * PS + tx * TN + v] =
                     make_float4(acc[u][v], acc[u][v + 1], acc[u][v + 2], acc[u][v + 3]);
         __syncthreads();
-        epi_readout(tb, stg, e, tile_base(e, rt, ct), E, tid, NT);
+        epi_readout(tb, stg, e, tile_base(e, rt, ct), E, tid, NT, gather_mode(e.lowCc));
         __syncthreads();
     }
 }

@@ -33,9 +33,10 @@ namespace tqc {
 namespace {
 
 constexpr int BM = 128;
-constexpr int EPI_WARPS = 8;
+constexpr int EPI_WARPS = 16;
 constexpr int EPI_THREADS = 32 * EPI_WARPS;
 constexpr int NTHREADS = 64 + EPI_THREADS;
+constexpr int STAGE_WARPS = 8;  // epilogue warpgroups 0 and 1 move accumulators out of TMEM
 constexpr long long WAIT_CYCLES = 4000000000ll;  // about 2 s at the boost clock
 
 enum Kind { K_BF16 = 0, K_BF16X3 = 1, K_TF32 = 2 };
@@ -44,7 +45,8 @@ struct UmmaParams {
     int64_t n_tiles;
     int64_t col_tiles;
     int32_t k_blocks;
-    int32_t rowmajor;  // staging orientation (1: the result's lowest bit is a column bit)
+    int32_t rowmajor;  // staging orientation (pick_staging)
+    int32_t gmode;     // gather mode of the write-out (pick_staging)
     EpiParams epi;
     int *err;
 };
@@ -58,10 +60,12 @@ struct Cfg {
     static constexpr int B_BYTES = BN * 128;
     static constexpr int STAGE_BYTES = PLANES * (A_BYTES + B_BYTES);
     static constexpr int STAGES = KIND == K_BF16X3 ? 2 : (BN == 64 ? 6 : 4);
-    static constexpr int PITCH_R = BN + 4;         // row-major staging pitch (floats)
+    static constexpr int SUB_N = 64;               // epilogue sub-tile: 128 x 64
+    static constexpr int PITCH_R = SUB_N + 4;      // row-major staging pitch (floats)
     static constexpr int PITCH_C = BM + 4;         // column-major staging pitch
-    static constexpr int STG_BYTES = (BM * PITCH_R > BN * PITCH_C ? BM * PITCH_R : BN * PITCH_C) * 4;
-    static constexpr int BAR_BYTES = 256;
+    static constexpr int STG_FLOATS = BM * PITCH_R > SUB_N * PITCH_C ? BM * PITCH_R : SUB_N * PITCH_C;
+    static constexpr int STG_BYTES = 2 * STG_FLOATS * 4;  // two buffers (ping-pong)
+    static constexpr int BAR_BYTES = 512;
     static constexpr int SMEM = 1024 + STAGES * STAGE_BYTES + STG_BYTES + (int)sizeof(EpiTables) + BAR_BYTES;
     static constexpr int TMEM_COLS = 2 * BN;
     // instruction descriptor: D = F32, A/B = BF16 (1) or TF32 (2), K-major, N >> 3, M >> 4
@@ -144,6 +148,18 @@ __device__ __forceinline__ void umma_commit(uint64_t *bar) {
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
+// Named barrier 1 over the epilogue threads that also ORs a predicate across
+// them, so every thread takes the same stop decision.
+__device__ __forceinline__ bool epi_barrier_or(int nthreads, bool pred) {
+    uint32_t r;
+    asm volatile(
+        "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, 1, %2, p;\n selp.u32 %0, 1, 0, q;\n}\n"
+        : "=r"(r)
+        : "r"((uint32_t)pred), "r"(nthreads)
+        : "memory");
+    return r != 0;
+}
+
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
@@ -175,6 +191,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     uint64_t *drain = tempty + 2;
     uint32_t *tmem_slot = (uint32_t *)(drain + 1);
     volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
+    uint64_t *tile_base_slot = (uint64_t *)(tmem_slot + 2);  // epilogue: base offsets of two sub-tiles
+    uint8_t *tb_pos = (uint8_t *)(tile_base_slot + 2);       // epilogue: tile-index bit positions
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
@@ -184,7 +202,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         }
         for (int a = 0; a < 2; ++a) {
             mbar_init(&tfull[a], 1);
-            mbar_init(&tempty[a], EPI_WARPS);
+            mbar_init(&tempty[a], STAGE_WARPS);
         }
         mbar_init(drain, 1);
         *abort_flag = 0;
@@ -285,51 +303,154 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         }
     } else {
         // ------------------------------------------------ epilogue
-        // two warpgroups: each reads all 128 TMEM lanes for half of the columns
+        // Software pipeline over 128 x 64 sub-tiles (BN / 64 per MMA tile):
+        // iteration k writes sub-tile k out of one staging buffer while the
+        // staging warps (warpgroups 0 and 1, one 32-column chunk each) move
+        // sub-tile k+1 from TMEM into the other buffer.
+        constexpr int SUBS = BN / C::SUB_N;
+        const int wg = (warp - 2) >> 2;         // warpgroup 0..3
         const int lane_grp = warp & 3;          // TMEM lanes this warp may read
-        const int half = (warp - 2) >> 2;       // column half of this warpgroup
         const int row = lane_grp * 32 + lane;   // accumulator row
-        const int etid = threadIdx.x - 64;      // 0..255
+        const int etid = threadIdx.x - 64;      // 0..EPI_THREADS-1
         const int Me = 1 << e.a_bits, Ne = 1 << e.b_bits;
         const int E = Me * Ne;
-        epi_tables_init(tb, e, P.rowmajor != 0, P.rowmajor ? C::PITCH_R : C::PITCH_C, etid, EPI_THREADS);
+        const int pitch = P.rowmajor ? C::PITCH_R : C::PITCH_C;
+        float *stgbuf[2] = {stg, stg + C::STG_FLOATS};
+        epi_tables_init(tb, e, P.rowmajor != 0, pitch, etid, EPI_THREADS);
+        // bit positions of the result bits that carry the tile indices
+        int8_t(*pos)[64] = (int8_t(*)[64])tb_pos;
+        int *npos = (int *)(tb_pos + 128);
+        if (etid < 2) {
+            uint64_t m = etid == 0 ? e.highR : e.highC;
+            int n = 0;
+            while (m) {
+                pos[etid][n++] = (int8_t)__ffsll((long long)m) - 1;
+                m &= m - 1;
+            }
+            npos[etid] = n;
+        }
         asm volatile("bar.sync 1, %0;" ::"n"(EPI_THREADS) : "memory");
-        int64_t lt = 0;
-        for (int64_t tile = blockIdx.x; tile < P.n_tiles; tile += gridDim.x, ++lt) {
+        // Full sub-tiles: the staging and destination offsets of this thread's
+        // runs are the same for every sub-tile, so they live in registers.
+        constexpr int ITERS = BM * C::SUB_N / (4 * EPI_THREADS);
+        const bool reg_path = E == BM * C::SUB_N && e.L >= 2 && P.gmode != G_SCALAR && (e.tileMask >> 32) == 0;
+        uint32_t r_s0[ITERS], r_s1[ITERS], r_g[ITERS];
+        if (reg_path) {
+#pragma unroll
+            for (int it = 0; it < ITERS; ++it) {
+                const int t = (etid + it * EPI_THREADS) * 4;
+                const uint32_t sh = tb->s_hi[t >> 7];
+                const int tl = t & 127;
+                r_s0[it] = sh + tb->s_lo[tl];
+                r_s1[it] = sh + tb->s_lo[tl + (P.gmode == G_PAIR01 ? 2 : 1)];
+                r_g[it] = (uint32_t)(tb->g_hi[t >> 7] + tb->g_lo[tl]);
+            }
+        }
+        const double sc = (e.mode == EPI_OUT_F32 || e.mode == EPI_OUT_F64) ? e.zinfo[1] : 1.0;
+        const int64_t my_tiles =
+            (int64_t)blockIdx.x < P.n_tiles ? (P.n_tiles - 1 - (int64_t)blockIdx.x) / gridDim.x + 1 : 0;
+        const int64_t n_sub = my_tiles * SUBS;
+        // stage sub-tile k into buffer k & 1 (staging warps only); returns false on abort
+        auto stage_sub = [&](int64_t k) {
+            const int64_t lt = k / SUBS;
+            const int h = (int)(k % SUBS);
             const int acc = (int)(lt & 1);
-            const uint32_t aph = (uint32_t)((lt >> 1) & 1);
-            mbar_wait(&tfull[acc], aph, abort_flag);
-            asm volatile("bar.sync 1, %0;" ::"n"(EPI_THREADS) : "memory");
-            if (*abort_flag) break;
-            tc_fence_after();
-            const uint32_t tbase = tmem_base + ((uint32_t)(lane_grp * 32) << 16) + (uint32_t)(acc * BN);
-#pragma unroll 1
-            for (int ch = half * (BN / 64); ch < (half + 1) * (BN / 64); ++ch) {
-                uint32_t r[32];
-                tmem_ld32(tbase + ch * 32, r);
-                if (row < Me) {
-                    if (P.rowmajor) {
-                        float *dst = stg + row * C::PITCH_R + ch * 32;
+            if (h == 0) {
+                if (lane == 0) mbar_wait(&tfull[acc], (uint32_t)((lt >> 1) & 1), abort_flag);
+                __syncwarp();
+                tc_fence_after();
+            }
+            if (*abort_flag) return;
+            float *sb = stgbuf[k & 1];
+            const int col0 = wg * 32;  // column chunk of this warpgroup inside the sub-tile
+            uint32_t r[32];
+            tmem_ld32(tmem_base + ((uint32_t)(lane_grp * 32) << 16) + (uint32_t)(acc * BN + h * C::SUB_N + col0), r);
+            if (row < Me) {
+                if (P.rowmajor) {
+                    float *dst = sb + row * C::PITCH_R + col0;
 #pragma unroll
-                        for (int j = 0; j < 32; j += 4)
-                            if (ch * 32 + j < Ne)
-                                *(float4 *)(dst + j) = make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]),
-                                                                   __uint_as_float(r[j + 2]), __uint_as_float(r[j + 3]));
-                    } else {
+                    for (int j = 0; j < 32; j += 4)
+                        if (col0 + j < Ne)
+                            *(float4 *)(dst + j) = make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]),
+                                                               __uint_as_float(r[j + 2]), __uint_as_float(r[j + 3]));
+                } else {
 #pragma unroll
-                        for (int j = 0; j < 32; ++j)
-                            if (ch * 32 + j < Ne) stg[(ch * 32 + j) * C::PITCH_C + row] = __uint_as_float(r[j]);
-                    }
+                    for (int j = 0; j < 32; ++j)
+                        if (col0 + j < Ne) sb[(col0 + j) * C::PITCH_C + row] = __uint_as_float(r[j]);
                 }
             }
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&tempty[acc]);
-            asm volatile("bar.sync 1, %0;" ::"n"(EPI_THREADS) : "memory");
-            const int64_t rt = tile / P.col_tiles;
-            const int64_t ct = tile - rt * P.col_tiles;
-            epi_readout(tb, stg, e, tile_base(e, (uint64_t)rt, (uint64_t)ct), E, etid, EPI_THREADS);
-            asm volatile("bar.sync 1, %0;" ::"n"(EPI_THREADS) : "memory");
+            if (h == SUBS - 1) {  // last read of this accumulator by this warp
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&tempty[acc]);
+            }
+        };
+        // Base offset of a sub-tile, computed by one warp: lane l deposits bit
+        // l (and l + 32) of the row / column tile index, then an OR reduction.
+        auto sub_base_warp = [&](int64_t k) {
+            const int64_t tile = (int64_t)blockIdx.x + (k / SUBS) * gridDim.x;
+            const uint64_t rt = (uint64_t)(tile / P.col_tiles);
+            const uint64_t ct = (uint64_t)((tile - (int64_t)rt * P.col_tiles) * SUBS + k % SUBS);
+            uint64_t v = 0;
+#pragma unroll
+            for (int hw = 0; hw < 2; ++hw) {
+                const int b = lane + 32 * hw;
+                if (b < npos[0] && ((rt >> b) & 1)) v |= 1ull << pos[0][b];
+                if (b < npos[1] && ((ct >> b) & 1)) v |= 1ull << pos[1][b];
+            }
+            const uint32_t lo = __reduce_or_sync(0xffffffffu, (uint32_t)v);
+            const uint32_t hi = __reduce_or_sync(0xffffffffu, (uint32_t)(v >> 32));
+            return ((uint64_t)hi << 32) | lo;
+        };
+        if (n_sub > 0) {
+            if (wg < 2) stage_sub(0);
+            if (etid < 32) {
+                const uint64_t b = sub_base_warp(0);
+                if (etid == 0) tile_base_slot[0] = b;
+            }
+        }
+        bool stop = epi_barrier_or(EPI_THREADS, *abort_flag != 0);
+        for (int64_t k = 0; k < n_sub && !stop; ++k) {
+            if (k + 1 < n_sub) {
+                if (wg < 2) stage_sub(k + 1);
+                if (etid < 32) {
+                    const uint64_t b = sub_base_warp(k + 1);
+                    if (etid == 0) tile_base_slot[(k + 1) & 1] = b;
+                }
+            }
+            const float *cur = stgbuf[k & 1];
+            const uint64_t base = tile_base_slot[k & 1];
+            if (reg_path) {
+#pragma unroll
+                for (int it = 0; it < ITERS; ++it) {
+                    float v[4];
+                    if (P.gmode == G_VEC4) {
+                        const float4 q = *(const float4 *)(cur + r_s0[it]);
+                        v[0] = q.x;
+                        v[1] = q.y;
+                        v[2] = q.z;
+                        v[3] = q.w;
+                    } else {
+                        const float2 a = *(const float2 *)(cur + r_s0[it]);
+                        const float2 b = *(const float2 *)(cur + r_s1[it]);
+                        if (P.gmode == G_PAIR01) {
+                            v[0] = a.x;
+                            v[1] = a.y;
+                            v[2] = b.x;
+                            v[3] = b.y;
+                        } else {
+                            v[0] = a.x;
+                            v[1] = b.x;
+                            v[2] = a.y;
+                            v[3] = b.y;
+                        }
+                    }
+                    store_run_f32(e, base + r_g[it], v, 4, sc);
+                }
+            } else {
+                epi_readout(tb, cur, e, base, E, etid, EPI_THREADS, P.gmode);
+            }
+            stop = epi_barrier_or(EPI_THREADS, *abort_flag != 0);
         }
     }
     __syncthreads();
@@ -397,11 +518,16 @@ cudaError_t launch_kind(const StepArgs &a, int *d_err, cudaStream_t s) {
     }
     UmmaParams p;
     p.epi = a.epi;
+    // MMA tiles are 128 x BN; the epilogue parameters describe 128 x 64 sub-tiles
+    const int lbn = BN == 128 ? 7 : 6;
+    if (BN == 128 && a.nb < 7) return cudaErrorInvalidValue;
     const int64_t row_tiles = (int64_t)1 << (a.mb - a.epi.a_bits);
-    p.col_tiles = (int64_t)1 << (a.nb - a.epi.b_bits);
+    p.col_tiles = a.nb >= lbn ? (int64_t)1 << (a.nb - lbn) : 1;
     p.n_tiles = row_tiles * p.col_tiles;
     p.k_blocks = (int)(K / C::BK);
-    p.rowmajor = (a.epi.lowCc & 1u) ? 1 : 0;
+    const StagePick pk = pick_staging(a.epi.lowRc, a.epi.lowCc);
+    p.rowmajor = pk.rowmajor;
+    p.gmode = pk.gmode;
     p.err = d_err;
     const int64_t grid = std::min<int64_t>(p.n_tiles, sm_count());
     umma_step_kernel<BN, KIND><<<(unsigned)grid, NTHREADS, C::SMEM, s>>>(tA, tB, tAl, tBl, p);
@@ -420,7 +546,11 @@ cudaError_t launch_bn(int prec, const StepArgs &a, int *d_err, cudaStream_t s) {
 
 }  // namespace
 
-TileShape umma_tile(int cfg) { return cfg == UMMA_128x64 ? TileShape{7, 6} : TileShape{7, 7}; }
+// Epilogue tile of both configurations (the MMA tile is 128 x 128 or 128 x 64).
+TileShape umma_tile(int cfg) {
+    (void)cfg;
+    return TileShape{7, 6};
+}
 
 cudaError_t launch_umma_step(int cfg, int prec, const StepArgs &a, int *d_err, cudaStream_t s) {
     if (cfg == UMMA_128x64) return launch_bn<64>(prec, a, d_err, s);
