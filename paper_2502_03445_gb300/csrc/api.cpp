@@ -151,6 +151,7 @@ tqc_status tqc_network_upload(tqc_net_t net, int32_t sub, int32_t dtype, const v
     size_t bytes = (size_t)nd.elems * (nd.dtype == TQC_F64 ? 8 : 4);
     cudaError_t e = cudaMemcpyAsync(nd.d_data, host_data, bytes, cudaMemcpyHostToDevice, (cudaStream_t)stream);
     if (e != cudaSuccess) return fail(TQC_ERR_CUDA, std::string("upload: ") + cudaGetErrorString(e));
+    n.version++;
     return TQC_OK;
 }
 
@@ -247,6 +248,7 @@ tqc_status tqc_contract_host(tqc_plan_t plan, const void *const *host_tensors, i
                 size_t bytes = (size_t)nd.elems * (nd.dtype == TQC_F64 ? 8 : 4);
                 cudaError_t e = cudaMemcpyAsync(nd.d_data, host_tensors[j], bytes, cudaMemcpyHostToDevice, s);
                 if (e != cudaSuccess) return fail(TQC_ERR_CUDA, std::string("upload: ") + cudaGetErrorString(e));
+                p.net->version++;
             }
     int64_t ob = p.out_elems() * (out_dtype == TQC_F64 ? 8 : 4);
     if (p.d_hostout_bytes < ob) {

@@ -207,7 +207,10 @@ tqc_status exec_contract(Plan *p, const uint8_t *fixed_bits, void *d_out, int ou
     const int nE = p->net->n_cuts;
     double *zslice = (double *)ws_ptr(p->d_zws, p->zws_bytes);
 
-    // ---- total mass Z (scalar network: every output summed), FP64
+    // ---- total mass Z (scalar network: every output summed), FP64.  Z depends
+    // on the tensors only, so it is recomputed when they changed since the
+    // plan last computed it.
+    if (p->z_version != p->net->version) {
     for (int64_t sl = 0; sl < ns; ++sl) {
         for (int j = 0; j < p->m; ++j) {
             const TensorPlan &t = p->ztensors[j];
@@ -224,6 +227,8 @@ tqc_status exec_contract(Plan *p, const uint8_t *fixed_bits, void *d_out, int ou
         }
     }
     TQC_CUDA(launch_zfinal(zslice, (int)ns, nE, !(p->flags & TQC_FLAG_NO_RENORM), p->d_zinfo, s), "zfinal");
+    p->z_version = p->net->version;
+    }
 
     // ---- single subcircuit: the bin is a gather of its tensor
     if (p->m == 1) {

@@ -116,6 +116,8 @@ extern "C" tqc_status tqc_contract_noalloc(tqc_plan_t plan, const void *const *d
     void *sv_ws = p.d_ws, *sv_zws = p.d_zws;
     double *sv_zinfo = p.d_zinfo;
     const bool sv_ready = p.ready;
+    const uint64_t sv_zver = p.z_version;
+    p.z_version = 0;  // the caller's tensors: always compute the total mass
     const int sv_profile = p.profile;
     const int sv_device = net.device;
     for (size_t i = 0; i < p.steps.size(); ++i) sv_tiles[i] = p.steps[i].tile;
@@ -139,6 +141,7 @@ extern "C" tqc_status tqc_contract_noalloc(tqc_plan_t plan, const void *const *d
     p.d_zws = sv_zws;
     p.d_zinfo = sv_zinfo;
     p.ready = sv_ready;
+    p.z_version = sv_zver;
     p.profile = sv_profile;
     net.device = sv_device;
     for (size_t i = 0; i < p.steps.size(); ++i) p.steps[i].tile = sv_tiles[i];

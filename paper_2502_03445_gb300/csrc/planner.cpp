@@ -616,14 +616,17 @@ tqc_status build_plan(Net *net, const tqc_plan_opts &o, Plan *p) {
     }
     os << "],\"layouts\":[";
     for (size_t i = 0; i < p->tensors.size(); ++i) os << (i ? "," : "") << mode_str(p->tensors[i].layout);
-    int64_t launches = ((int64_t)p->m + (int64_t)p->zsteps.size()) * p->n_slices() + 1;
+    // kernel launches of one contract once the total mass is cached, and of
+    // the total-mass network when the tensors changed
+    const int64_t z_launches = ((int64_t)p->m + (int64_t)p->zsteps.size()) * p->n_slices() + 1;
+    int64_t launches = 0;
     if (p->m == 1) launches += 1;
     else {
         for (int j = 0; j < p->m; ++j) launches += p->tensors[j].slice_dep ? p->n_slices() : 1;
         for (auto &st : p->steps) launches += p->tensors[st.c].slice_dep ? p->n_slices() : 1;
         if (p->n_slices() > 1) launches += 1;
     }
-    os << "],\"launches_per_contract\":" << launches;
+    os << "],\"launches_per_contract\":" << launches << ",\"total_mass_launches\":" << z_launches;
     char buf[256];
     std::snprintf(buf, sizeof buf, ",\"flops\":%.6g,\"bytes\":%.6g,\"predicted_s\":%.6g,\"ws_bytes\":%lld}", p->flops,
                   p->bytes, p->predicted_s, (long long)p->ws_bytes);

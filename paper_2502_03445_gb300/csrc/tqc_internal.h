@@ -33,6 +33,7 @@ struct Net {
     bool has_data = false;
     int device = 0;
     int live_plans = 0;
+    uint64_t version = 1;  // bumped whenever tensor data changes
 };
 
 // ---------------------------------------------------------------- layouts
@@ -142,6 +143,7 @@ struct Plan {
     bool ready = false;
     int tuned = 0;
     int profile = 0;
+    uint64_t z_version = 0;                // network version the cached Z belongs to
     std::vector<std::vector<std::array<void *, 2>>> step_events;  // per step: (start, stop) cudaEvent_t
     int64_t n_slices() const { return (int64_t)1 << (2 * sliced.size()); }
     int64_t out_elems() const { return (int64_t)1 << free_qubits.size(); }

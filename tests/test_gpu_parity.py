@@ -294,3 +294,22 @@ def test_tensor_core_sliced():
     got, z, d = run(net, precision="bf16x3", sliced=[1, 6])
     assert d["sliced"] == [1, 6]
     check_fp32(got, want)
+
+
+def test_total_mass_tracks_uploads():
+    """Z is cached per plan and recomputed after new tensors arrive."""
+    base = small_pp(740, n=12, m=3, cuts=5)
+    nets = [tensors.random_data_network(base, s) for s in (1, 2)]
+    h = tqc.Network(nets[0])
+    p = tqc.Plan(h, precision="fp32")
+    out = torch.empty(p.out_elems, dtype=torch.float32, device="cuda")
+    for rep, net in enumerate([nets[0], nets[0], nets[1], nets[1]]):
+        if rep == 2:
+            for j, nd in enumerate(net.nodes):
+                h.upload(j, nd.data)
+        z = p.contract(out, want_z=True)
+        z_or = oracle.total_mass(net)
+        assert abs(z - z_or) <= 1e-9 * abs(z_or), (rep, z, z_or)
+        check_fp32(out.cpu().numpy().astype(np.float64), oracle.recon_bin(net), z_or)
+    p.close()
+    h.close()
