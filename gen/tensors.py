@@ -231,3 +231,24 @@ def random_data_network(net: Network, seed: int) -> Network:
     nodes = [Node(nd.out_qubits, nd.cut_ids, nd.cut_role, rng.standard_normal(nd.data.size))
              for nd in net.nodes]
     return Network(net.n_qubits, net.n_cuts, nodes, {"kind": "gaussian", "seed": seed})
+
+
+def random_shape_network(n_qubits: int, m: int, n_cuts: int, w_max: int, seed: int,
+                         max_node_cuts: int | None = None) -> Network:
+    """Shape-matched network with i.i.d. N(0,1) FP32-valued entries: fast to
+    draw at sizes where only timing matters (cost-model training data)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    edges, outs = sample_shape(n_qubits, m, n_cuts, w_max, rng, max_node_cuts)
+    cuts = [[] for _ in range(m)]
+    for cid, (a, b) in enumerate(edges):
+        cuts[a].append((cid, 0))
+        cuts[b].append((cid, 1))
+    nodes = []
+    for j in range(m):
+        cl = sorted(cuts[j])
+        size = (4 ** len(cl)) << len(outs[j])
+        nodes.append(Node(list(outs[j]), [c for c, _ in cl], [r for _, r in cl],
+                          rng.standard_normal(size, dtype=np.float32).astype(np.float64)))
+    net = Network(n_qubits, n_cuts, nodes, {"kind": "gaussian-shape", "seed": seed, "edges": edges})
+    net.check()
+    return net

@@ -252,6 +252,51 @@ TQC_API tqc_status tqc_contract_noalloc(tqc_plan_t plan, const void *const *d_te
                                         void *cuda_stream);
 TQC_API int64_t tqc_noalloc_scratch_bytes(void);
 
+/*
+ * Learned cost model (replaces the FLOP-count estimate of Eq.
+ * classical_runtime, §V, which the paper finds consistently high).  A
+ * multilayer perceptron, 3 hidden layers of 128 ReLU units, maps a plan's
+ * TQC_PLAN_FEATURES features (tqc_plan_features) to the log of its measured
+ * contraction time in seconds.  Forward, backward and Adam run in the
+ * library's CUDA kernels on the current device (FP32); calls synchronise.
+ *
+ * Parameter layout (flat): W1 [F x 128], b1 [128], W2 [128 x 128], b2,
+ * W3 [128 x 128], b3, W4 [128 x 1], b4; rows of X are samples, Y = X W + b.
+ */
+#define TQC_PLAN_FEATURES 32
+typedef struct tqc_costmodel *tqc_costmodel_t;
+
+/* New model with He-uniform weights from a seeded generator, zero biases. */
+TQC_API tqc_status tqc_costmodel_create(int32_t n_features, uint64_t seed, tqc_costmodel_t *out);
+TQC_API tqc_status tqc_costmodel_destroy(tqc_costmodel_t model);
+/* Copy the parameters out (h_out == NULL: only report the count in *n). */
+TQC_API tqc_status tqc_costmodel_params(tqc_costmodel_t model, float *h_out, int32_t *n);
+TQC_API tqc_status tqc_costmodel_set_params(tqc_costmodel_t model, const float *h_in, int32_t n);
+/* Mean squared error of the raw network on (X [n x F], t [n]) and its
+ * gradient w.r.t. the flat parameters (no standardisation applied). */
+TQC_API tqc_status tqc_costmodel_grad(tqc_costmodel_t model, const float *h_X, const float *h_t, int32_t n,
+                                      float *h_grad, float *h_loss);
+/* Fit log-times: standardises features and labels (statistics kept with the
+ * model), then `epochs` passes of Adam (lr, beta 0.9/0.999) over shuffled
+ * minibatches; *final_loss = mean standardised MSE of the last epoch. */
+TQC_API tqc_status tqc_costmodel_train(tqc_costmodel_t model, const float *h_X, const float *h_logt, int32_t n,
+                                       int32_t epochs, int32_t batch, float lr, uint64_t seed, float *final_loss);
+/* Predicted log-times (seconds) of n feature rows. */
+TQC_API tqc_status tqc_costmodel_predict(tqc_costmodel_t model, const float *h_X, int32_t n, float *h_logt);
+TQC_API tqc_status tqc_costmodel_save(tqc_costmodel_t model, const char *path);
+TQC_API tqc_status tqc_costmodel_load(const char *path, tqc_costmodel_t *out);
+
+/* The TQC_PLAN_FEATURES features of a plan (n must be >= TQC_PLAN_FEATURES). */
+TQC_API tqc_status tqc_plan_features(tqc_plan_t plan, float *out, int32_t n);
+/*
+ * Candidate contraction orders the learned planner ranks: the optima of the
+ * time, multiply-add and byte models, the greedy order, then seeded random
+ * trees.  orders receives up to max_n orders of n_sub-1 (a, b) pairs each in
+ * the SSA form of tqc_plan_opts.order; *n_out = number written.
+ */
+TQC_API tqc_status tqc_plan_candidates(tqc_net_t net, const tqc_plan_opts *opts, int32_t max_n, int32_t *orders,
+                                       int32_t *n_out);
+
 /* Thread-local description of the last error ("" if none). */
 TQC_API const char *tqc_last_error(void);
 

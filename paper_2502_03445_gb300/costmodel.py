@@ -1,0 +1,58 @@
+"""Training data for the learned cost model: timings the planner generates.
+
+For each network, the planner's candidate contraction orders
+(:func:`tqc.plan_candidates`) are planned and timed on the GPU with CUDA
+events; each timing is paired with the plan's features.  The model
+(:class:`tqc.CostModel`) is then trained on the log of the measured seconds
+and used by ``Plan(..., planner=tqc.PLANNER_LEARNED, costmodel_path=...)`` to
+rank candidates.  All device work goes through libtqc."""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+from . import tqc
+
+
+def time_plan(plan: "tqc.Plan", out, reps: int = 3, warmup: int = 1) -> float:
+    """Median seconds of ``plan.contract(out)`` over ``reps`` runs."""
+    import torch
+    for _ in range(warmup):
+        plan.contract(out)
+    ts = []
+    for _ in range(reps):
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record()
+        plan.contract(out)
+        e.record()
+        e.synchronize()
+        ts.append(s.elapsed_time(e) / 1e3)
+    return float(np.median(ts))
+
+
+def collect(handle: "tqc.Network", precision="auto", free_qubits=None, max_candidates: int = 10, reps: int = 3):
+    """Time every candidate plan of one network.
+
+    Returns a list of records ``{"order", "features", "seconds",
+    "predicted_s", "flops"}`` (``predicted_s`` is the analytic model's
+    estimate, the planner's own judge)."""
+    import torch
+    recs = []
+    orders = tqc.plan_candidates(handle, max_candidates, precision=precision, free_qubits=free_qubits)
+    n_out = 1 << (handle.n_qubits if free_qubits is None else len(free_qubits))
+    out = torch.empty(n_out, dtype=torch.float32, device="cuda")
+    for od in orders:
+        p = tqc.Plan(handle, precision=precision, order=od, free_qubits=free_qubits)
+        d = p.describe()
+        secs = time_plan(p, out, reps=reps)
+        recs.append({"order": od, "features": p.features(), "seconds": secs, "predicted_s": d["predicted_s"],
+                     "flops": d["flops"]})
+        p.close()
+    return recs
+
+
+def dataset(records):
+    X = np.stack([r["features"] for r in records]).astype(np.float32)
+    y = np.array([math.log(max(r["seconds"], 1e-9)) for r in records], np.float32)
+    return X, y

@@ -215,6 +215,7 @@ tqc_status tqc_plan_step(tqc_plan_t plan, int32_t step, int32_t *lm, int32_t *ln
 
 int32_t tqc_plan_describe(tqc_plan_t plan, char *buf, int32_t size) {
     if (!plan) return -1;
+    plan->p.describe_json = plan_describe(plan->p);
     const std::string &s = plan->p.describe_json;
     if (buf && size > 0) {
         size_t n = std::min((size_t)size - 1, s.size());
@@ -267,6 +268,37 @@ tqc_status tqc_contract_host(tqc_plan_t plan, const void *const *host_tensors, i
     if (e == cudaSuccess && z_out) e = cudaMemcpyAsync(z_out, p.d_zinfo, sizeof(double), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return fail(TQC_ERR_CUDA, std::string("result download: ") + cudaGetErrorString(e));
+    return TQC_OK;
+}
+
+tqc_status tqc_plan_features(tqc_plan_t plan, float *out, int32_t n) {
+    if (!plan || !out) return fail(TQC_ERR_INVALID, "NULL argument");
+    if (n < TQC_PLAN_FEATURES) return fail(TQC_ERR_INVALID, "feature buffer smaller than TQC_PLAN_FEATURES");
+    std::vector<double> f = plan_features(plan->p);
+    for (int i = 0; i < TQC_PLAN_FEATURES; ++i) out[i] = i < (int)f.size() ? (float)f[i] : 0.f;
+    return TQC_OK;
+}
+
+tqc_status tqc_plan_candidates(tqc_net_t net, const tqc_plan_opts *opts, int32_t max_n, int32_t *orders,
+                               int32_t *n_out) {
+    if (!net || !orders || !n_out || max_n < 1) return fail(TQC_ERR_INVALID, "bad candidate arguments");
+    tqc_plan_opts o;
+    tqc_plan_opts_default(&o);
+    if (opts) o = *opts;
+    std::vector<std::vector<int32_t>> c;
+    try {
+        c = plan_candidate_orders(&net->n, o, max_n);
+    } catch (const std::exception &ex) {
+        return fail(TQC_ERR_INVALID, std::string("candidates: ") + ex.what());
+    }
+    const int per = 2 * ((int)net->n.nodes.size() - 1);
+    int k = 0;
+    for (auto &ord : c) {
+        if (k >= max_n) break;
+        std::copy(ord.begin(), ord.end(), orders + (size_t)k * per);
+        ++k;
+    }
+    *n_out = k;
     return TQC_OK;
 }
 

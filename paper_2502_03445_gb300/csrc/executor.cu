@@ -11,7 +11,10 @@
 
 #include <algorithm>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
+#include <tuple>
 
 #include "launch.h"
 #include "tqc_internal.h"
@@ -123,7 +126,100 @@ tqc_status launch_step(const Plan &p, const StepPlan &st, StepArgs &a, int *d_er
 
 TileShape tile_of(const StepPlan &st) { return st.klass == KC_UMMA ? umma_tile(st.tile) : simt_tile(st.tile); }
 
+// ---------------------------------------------------------------- autotuner
+// For every step, time each tile configuration that fits the step on the
+// plan's own operands (CUDA events, best of three after one warm-up launch)
+// and keep the fastest.  Results are cached process-wide by the step's
+// shape and epilogue pattern, so equal steps of other plans reuse them.
+struct TuneKey {
+    int klass, prec, mb, nb, kb, mode;
+    uint64_t maskR, maskC;
+    bool operator<(const TuneKey &o) const {
+        return std::tie(klass, prec, mb, nb, kb, mode, maskR, maskC) <
+               std::tie(o.klass, o.prec, o.mb, o.nb, o.kb, o.mode, o.maskR, o.maskC);
+    }
+};
+std::map<TuneKey, int> g_tune_cache;
+std::mutex g_tune_mu;
+
+std::vector<int> tile_candidates(const StepPlan &st) {
+    std::vector<int> c;
+    if (st.klass == KC_UMMA) {
+        if (st.nb >= 7) c.push_back(UMMA_128x128);
+        c.push_back(UMMA_128x64);
+    } else {
+        c.push_back(SIMT_64x64);
+        if (st.mb >= 7 && st.nb >= 6) c.push_back(SIMT_128x64);
+        if (st.mb >= 7 && st.nb >= 7) c.push_back(SIMT_128x128);
+    }
+    return c;
+}
+
 }  // namespace
+
+tqc_status exec_autotune(Plan *p, void *d_out, int out_dtype, cudaStream_t s) {
+    const bool sliced = p->n_slices() > 1;
+    cudaEvent_t e0, e1;
+    TQC_CUDA(cudaEventCreate(&e0), "event");
+    TQC_CUDA(cudaEventCreate(&e1), "event");
+    int *d_err = (int *)(p->d_zinfo + 2);
+    tqc_status result = TQC_OK;
+    for (StepPlan &sp : p->steps) {
+        const TensorPlan &tc = p->tensors[sp.c];
+        int mode = sp.final ? (sliced ? EPI_F64_SET : (out_dtype == TQC_F64 ? EPI_OUT_F64 : EPI_OUT_F32))
+                            : epi_mode_of(tc.storage);
+        TuneKey key{sp.klass, sp.prec, sp.mb, sp.nb, sp.kb, mode, sp.maskR, sp.maskC};
+        {
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            auto it = g_tune_cache.find(key);
+            if (it != g_tune_cache.end()) {
+                sp.tile = it->second;
+                continue;
+            }
+        }
+        float best = 1e30f;
+        int best_tile = sp.tile;
+        for (int cand : tile_candidates(sp)) {
+            StepPlan trial = sp;
+            trial.tile = cand;
+            StepArgs a = step_args(*p, p->tensors, trial, p->d_ws, tile_of(trial));
+            a.epi.zinfo = p->d_zinfo;
+            a.epi.mode = mode;
+            if (sp.final) a.epi.out = sliced ? (out_dtype == TQC_F64 ? d_out : ws_ptr(p->d_ws, p->acc_offset)) : d_out;
+            else {
+                a.epi.out = ws_ptr(p->d_ws, tc.offset);
+                if (tc.storage == ST_BF16X2) a.epi.out_lo = ws_ptr(p->d_ws, tc.offset + tc.plane_bytes);
+            }
+            float ms_min = 1e30f;
+            for (int rep = 0; rep < 4 && result == TQC_OK; ++rep) {
+                cudaEventRecord(e0, s);
+                result = launch_step(*p, trial, a, d_err, s);
+                cudaEventRecord(e1, s);
+                if (result != TQC_OK) break;
+                if (cudaEventSynchronize(e1) != cudaSuccess) {
+                    result = fail(TQC_ERR_CUDA, "autotune timing");
+                    break;
+                }
+                float ms = 0;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (rep > 0) ms_min = std::min(ms_min, ms);
+            }
+            if (result != TQC_OK) break;
+            if (ms_min < best) {
+                best = ms_min;
+                best_tile = cand;
+            }
+        }
+        if (result != TQC_OK) break;
+        sp.tile = best_tile;
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune_cache[key] = best_tile;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (result == TQC_OK) p->tuned = 1;
+    return result;
+}
 
 tqc_status exec_prepare(Plan *p) {
     if (p->ready) return TQC_OK;
@@ -199,6 +295,10 @@ tqc_status exec_contract(Plan *p, const uint8_t *fixed_bits, void *d_out, int ou
     tqc_status st = exec_prepare(p);
     if (st != TQC_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
+    if (p->autotune && !p->tuned) {
+        st = exec_autotune(p, d_out, out_dtype, s);
+        if (st != TQC_OK) return st;
+    }
     const uint8_t *fixed = fixed_bits ? fixed_bits : p->fixed_bits.data();
     if (fixed_bits)
         for (int q = 0; q < p->net->n_qubits; ++q)

@@ -118,13 +118,18 @@ namespace {
 
 int effective_prec(int prec) { return prec == TQC_PREC_AUTO ? TQC_PREC_BF16X3 : prec; }
 
+// Step cost under one of three objectives: 0 = predicted time (default),
+// 1 = multiply-adds only (the paper's cost unit), 2 = HBM bytes only.
+thread_local int g_cost_mode = 0;
+
 double pair_time(const NetBits &nb, uint64_t x, uint64_t y, int prec, const CostConsts &cc) {
     StepShape s = pair_shape(subset_info(nb, x), subset_info(nb, y));
     int k = choose_class(s.mb, s.nb, s.kb, prec);
-    return step_cost(s.mb, s.nb, s.kb, k, prec, cc).time_s;
+    StepCost c = step_cost(s.mb, s.nb, s.kb, k, prec, cc);
+    return g_cost_mode == 1 ? c.macs : g_cost_mode == 2 ? c.bytes : c.time_s;
 }
 
-// Optimal tree for the additive step-time model by dynamic programming over
+// Optimal tree for the additive step-cost model by dynamic programming over
 // leaf subsets (every binary tree is reachable; 3^m work).
 std::vector<std::array<uint64_t, 2>> exhaustive_tree(const NetBits &nb, int prec, const CostConsts &cc) {
     int m = nb.m;
@@ -188,6 +193,76 @@ std::vector<std::array<uint64_t, 2>> greedy_tree(const NetBits &nb, int prec, co
         cur[bi] = merged;
     }
     return pairs;
+}
+
+uint64_t mix64(uint64_t &x) {
+    uint64_t z = (x += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// A random contraction tree: merge a uniformly drawn pair among those that
+// share a cut (any pair once none do).
+std::vector<std::array<uint64_t, 2>> random_tree(const NetBits &nb, uint64_t &rng) {
+    std::vector<uint64_t> cur;
+    for (int j = 0; j < nb.m; ++j) cur.push_back(1ull << j);
+    std::vector<std::array<uint64_t, 2>> pairs;
+    while (cur.size() > 1) {
+        std::vector<std::pair<int, int>> conn, all;
+        for (size_t i = 0; i < cur.size(); ++i)
+            for (size_t j = i + 1; j < cur.size(); ++j) {
+                all.push_back({(int)i, (int)j});
+                if (subset_info(nb, cur[i]).cuts & subset_info(nb, cur[j]).cuts) conn.push_back({(int)i, (int)j});
+            }
+        const auto &pool = conn.empty() ? all : conn;
+        auto pr = pool[mix64(rng) % pool.size()];
+        pairs.push_back({cur[pr.first], cur[pr.second]});
+        uint64_t merged = cur[pr.first] | cur[pr.second];
+        cur.erase(cur.begin() + pr.second);
+        cur[pr.first] = merged;
+    }
+    return pairs;
+}
+
+// Candidate trees for the learned planner: the optimum of the time, the
+// multiply-add and the byte models (dynamic programming, m <= 14), greedy on
+// the time model, then random trees; duplicates removed.
+std::vector<std::vector<std::array<uint64_t, 2>>> candidate_trees(const NetBits &nb, int prec, const CostConsts &cc,
+                                                                  int max_n, uint64_t seed) {
+    std::vector<std::vector<std::array<uint64_t, 2>>> out;
+    std::vector<std::vector<uint64_t>> seen;
+    auto add = [&](std::vector<std::array<uint64_t, 2>> t) {
+        std::vector<uint64_t> key;
+        for (auto &p : t) key.push_back(p[0] | p[1]);
+        std::sort(key.begin(), key.end());
+        if (std::find(seen.begin(), seen.end(), key) != seen.end()) return;
+        seen.push_back(key);
+        out.push_back(std::move(t));
+    };
+    if (nb.m <= 14)
+        for (int mode : {0, 1, 2}) {
+            g_cost_mode = mode;
+            add(exhaustive_tree(nb, prec, cc));
+        }
+    g_cost_mode = 0;
+    add(greedy_tree(nb, prec, cc));
+    uint64_t rng = seed;
+    for (int tries = 0; (int)out.size() < max_n && tries < 20 * max_n; ++tries) add(random_tree(nb, rng));
+    if ((int)out.size() > max_n) out.resize(max_n);
+    return out;
+}
+
+std::vector<int32_t> pairs_to_order(const std::vector<std::array<uint64_t, 2>> &pairs, int m) {
+    std::vector<uint64_t> sets;
+    for (int j = 0; j < m; ++j) sets.push_back(1ull << j);
+    std::vector<int32_t> ord;
+    for (auto &pr : pairs) {
+        ord.push_back((int32_t)(std::find(sets.begin(), sets.end(), pr[0]) - sets.begin()));
+        ord.push_back((int32_t)(std::find(sets.begin(), sets.end(), pr[1]) - sets.begin()));
+        sets.push_back(pr[0] | pr[1]);
+    }
+    return ord;
 }
 
 // SSA order (leaves 0..m-1, step s creates m+s) -> subset pairs
@@ -459,6 +534,75 @@ std::vector<double> plan_features(const Plan &p) {
     return f;
 }
 
+namespace {
+
+// Learned planner: plan every candidate tree completely (slicing, kernel
+// classes, layouts), predict each plan's log time with the cost model on the
+// GPU, keep the fastest.
+tqc_status learned_tree(Net *net, const tqc_plan_opts &o, const NetBits &nb, int prec, const CostConsts &cc,
+                        std::vector<std::array<uint64_t, 2>> *pairs, std::string *why) {
+    if (!o.costmodel_path) {
+        *why = "no cost-model path";
+        return TQC_ERR_INVALID;
+    }
+    tqc_costmodel *cm = nullptr;
+    if (costmodel_for_path(o.costmodel_path, &cm) != TQC_OK) {
+        *why = tqc_last_error();
+        return TQC_ERR_INVALID;
+    }
+    if (costmodel_n_in(cm) != (int)kPlanFeatures) {
+        *why = "cost model expects another feature count";
+        return TQC_ERR_INVALID;
+    }
+    auto cands = candidate_trees(nb, prec, cc, 24, 0x5EEDull + (uint64_t)nb.m);
+    std::vector<float> feats;
+    std::vector<int> ok;
+    for (size_t i = 0; i < cands.size(); ++i) {
+        std::vector<int32_t> ord = pairs_to_order(cands[i], nb.m);
+        tqc_plan_opts oc = o;
+        oc.order = ord.data();
+        oc.n_order = nb.m - 1;
+        oc.planner = TQC_PLANNER_GREEDY;
+        Plan cp;
+        if (build_plan(net, oc, &cp) != TQC_OK) continue;
+        for (double f : plan_features(cp)) feats.push_back((float)f);
+        ok.push_back((int)i);
+    }
+    if (ok.empty()) {
+        *why = "no valid candidate";
+        return TQC_ERR_INVALID;
+    }
+    std::vector<float> pred(ok.size());
+    if (costmodel_predict_host(cm, feats.data(), (int)ok.size(), pred.data()) != TQC_OK) {
+        *why = tqc_last_error();
+        return TQC_ERR_CUDA;
+    }
+    size_t best = std::min_element(pred.begin(), pred.end()) - pred.begin();
+    *pairs = cands[ok[best]];
+    return TQC_OK;
+}
+
+}  // namespace
+
+std::vector<std::vector<int32_t>> plan_candidate_orders(Net *net, const tqc_plan_opts &o, int max_n) {
+    Plan tmp;
+    tmp.net = net;
+    tmp.m = (int)net->nodes.size();
+    std::vector<char> isfree(net->n_qubits, 0);
+    for (int q = 0; q < net->n_qubits; ++q)
+        isfree[q] = !o.use_free_mask || (q < 64 ? (o.free_mask_lo >> q & 1) : (o.free_mask_hi >> (q - 64) & 1));
+    for (int q = 0; q < net->n_qubits; ++q)
+        if (isfree[q]) tmp.free_qubits.push_back(q);
+    for (int i = 0; i < o.n_sliced; ++i) tmp.sliced.push_back(o.sliced_cuts[i]);
+    NetBits nb = net_bits(tmp);
+    CostConsts cc;
+    std::vector<std::vector<int32_t>> out;
+    if (tmp.m < 2) return out;
+    for (auto &c : candidate_trees(nb, effective_prec(o.precision), cc, max_n, 0x5EEDull + (uint64_t)nb.m))
+        out.push_back(pairs_to_order(c, tmp.m));
+    return out;
+}
+
 tqc_status build_plan(Net *net, const tqc_plan_opts &o, Plan *p) {
     p->net = net;
     p->m = (int)net->nodes.size();
@@ -508,13 +652,27 @@ tqc_status build_plan(Net *net, const tqc_plan_opts &o, Plan *p) {
             for (int i = 0; i < o.n_order; ++i) ord.push_back({o.order[2 * i], o.order[2 * i + 1]});
             tqc_status st = order_to_pairs(ord, p->m, &pairs);
             if (st != TQC_OK) return st;
+            p->planner_used = "given";
         } else {
             int pl = o.planner;
-            if (pl == TQC_PLANNER_AUTO || pl == TQC_PLANNER_LEARNED) pl = p->m <= 8 ? TQC_PLANNER_EXHAUSTIVE : TQC_PLANNER_GREEDY;
-            if (pl == TQC_PLANNER_EXHAUSTIVE && p->m > 14)
-                return fail(TQC_ERR_UNSUPPORTED, "exhaustive planner limited to 14 subcircuits");
-            pairs = pl == TQC_PLANNER_EXHAUSTIVE ? exhaustive_tree(nb, prec, cc) : greedy_tree(nb, prec, cc);
+            std::string prefix;
+            if (pl == TQC_PLANNER_LEARNED) {
+                // rank candidate plans with the learned cost model; the
+                // exhaustive / greedy planner is the fallback
+                std::string why;
+                if (learned_tree(net, o, nb, prec, cc, &pairs, &why) == TQC_OK) p->planner_used = "learned";
+                else prefix = "fallback (" + why + "): ";
+            }
+            if (pairs.empty()) {
+                if (pl == TQC_PLANNER_AUTO || pl == TQC_PLANNER_LEARNED) pl = p->m <= 8 ? TQC_PLANNER_EXHAUSTIVE : TQC_PLANNER_GREEDY;
+                if (pl == TQC_PLANNER_EXHAUSTIVE && p->m > 14)
+                    return fail(TQC_ERR_UNSUPPORTED, "exhaustive planner limited to 14 subcircuits");
+                pairs = pl == TQC_PLANNER_EXHAUSTIVE ? exhaustive_tree(nb, prec, cc) : greedy_tree(nb, prec, cc);
+                p->planner_used = prefix + (pl == TQC_PLANNER_EXHAUSTIVE ? "exhaustive" : "greedy");
+            }
         }
+    } else {
+        p->planner_used = "single";
     }
 
     // two-tier slicing: inputs first, then inputs + intermediates + FP64 sum
@@ -598,9 +756,18 @@ tqc_status build_plan(Net *net, const tqc_plan_opts &o, Plan *p) {
         p->bytes += e * (8.0 + storage_bytes(p->tensors[j].storage)) * (p->tensors[j].slice_dep ? ns : 1.0);
     }
 
+    p->describe_json = plan_describe(*p);
+    return TQC_OK;
+}
+
+// Plan summary as JSON (current state: tiles reflect the autotuner once run).
+std::string plan_describe(const Plan &pl) {
+    const Plan *p = &pl;
+    const Net *net = p->net;
     std::ostringstream os;
     os << "{\"m\":" << p->m << ",\"n_qubits\":" << net->n_qubits << ",\"n_cuts\":" << net->n_cuts
-       << ",\"free\":" << p->free_qubits.size() << ",\"precision\":\"" << prec_name(prec) << "\",\"sliced\":[";
+       << ",\"free\":" << p->free_qubits.size() << ",\"precision\":\"" << prec_name(p->precision)
+       << "\",\"planner\":\"" << p->planner_used << "\",\"tuned\":" << p->tuned << ",\"sliced\":[";
     for (size_t i = 0; i < p->sliced.size(); ++i) os << (i ? "," : "") << p->sliced[i];
     os << "],\"order\":[";
     for (size_t i = 0; i < p->order.size(); ++i)
@@ -612,7 +779,7 @@ tqc_status build_plan(Net *net, const tqc_plan_opts &o, Plan *p) {
            << ",\"log2_n\":" << st.nb << ",\"log2_k\":" << st.kb << ",\"class\":\""
            << (st.klass == KC_UMMA ? "tcgen05" : "simt") << "\",\"prec\":\""
            << (st.klass == KC_UMMA ? prec_name(st.prec) : "fp32") << "\",\"out_layout\":" << mode_str(p->tensors[st.c].layout)
-           << ",\"mask_r\":" << st.maskR << ",\"mask_c\":" << st.maskC << "}";
+           << ",\"mask_r\":" << st.maskR << ",\"mask_c\":" << st.maskC << ",\"tile\":" << st.tile << "}";
     }
     os << "],\"layouts\":[";
     for (size_t i = 0; i < p->tensors.size(); ++i) os << (i ? "," : "") << mode_str(p->tensors[i].layout);
@@ -631,8 +798,7 @@ tqc_status build_plan(Net *net, const tqc_plan_opts &o, Plan *p) {
     std::snprintf(buf, sizeof buf, ",\"flops\":%.6g,\"bytes\":%.6g,\"predicted_s\":%.6g,\"ws_bytes\":%lld}", p->flops,
                   p->bytes, p->predicted_s, (long long)p->ws_bytes);
     os << buf;
-    p->describe_json = os.str();
-    return TQC_OK;
+    return os.str();
 }
 
 }  // namespace tqc

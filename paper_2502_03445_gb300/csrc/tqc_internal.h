@@ -9,6 +9,8 @@
 
 #include "tqc.h"
 
+struct tqc_costmodel;
+
 namespace tqc {
 
 // ---------------------------------------------------------------- errors
@@ -120,6 +122,7 @@ struct Plan {
     std::vector<uint8_t> fixed_bits;       // n_qubits
     int precision = TQC_PREC_FP32;
     int planner = TQC_PLANNER_GREEDY;
+    std::string planner_used;              // how the order was chosen
     int flags = 0;
     int autotune = 0;
     uint64_t budget = 0;
@@ -151,6 +154,14 @@ struct Plan {
 
 // planner entry points (planner.cpp)
 tqc_status build_plan(Net *net, const tqc_plan_opts &opts, Plan *plan);
+std::string plan_describe(const Plan &p);
+std::vector<std::vector<int32_t>> plan_candidate_orders(Net *net, const tqc_plan_opts &o, int max_n);
+
+// learned cost model (costmodel.cu)
+constexpr int kPlanFeatures = 32;
+tqc_status costmodel_for_path(const char *path, ::tqc_costmodel **out);
+tqc_status costmodel_predict_host(::tqc_costmodel *cm, const float *h_X, int n, float *h_y);
+int costmodel_n_in(::tqc_costmodel *cm);
 StepCost step_cost(int mb, int nb, int kb, int klass, int prec, const CostConsts &cc);
 std::vector<double> plan_features(const Plan &p);   // learned cost-model features
 int choose_class(int mb, int nb, int kb, int prec);

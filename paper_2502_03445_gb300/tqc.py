@@ -29,7 +29,11 @@ PREC_NAMES = {"fp32": PREC_FP32, "tf32": PREC_TF32, "bf16": PREC_BF16, "bf16x3":
 EXPORTS = ["tqc_network_create", "tqc_network_upload", "tqc_destroy", "tqc_plan_opts_default", "tqc_plan",
            "tqc_plan_info", "tqc_plan_step", "tqc_plan_describe", "tqc_contract", "tqc_contract_host",
            "tqc_contract_batch", "tqc_plan_profile", "tqc_plan_step_time", "tqc_plan_destroy", "tqc_last_error",
-           "tqc_contract_noalloc", "tqc_noalloc_scratch_bytes"]
+           "tqc_contract_noalloc", "tqc_noalloc_scratch_bytes", "tqc_costmodel_create", "tqc_costmodel_destroy",
+           "tqc_costmodel_params", "tqc_costmodel_set_params", "tqc_costmodel_grad", "tqc_costmodel_train",
+           "tqc_costmodel_predict", "tqc_costmodel_save", "tqc_costmodel_load", "tqc_plan_features",
+           "tqc_plan_candidates"]
+PLAN_FEATURES = 32
 
 
 class TqcError(RuntimeError):
@@ -86,6 +90,23 @@ def lib():
         L.tqc_contract_noalloc.restype = ctypes.c_int
         L.tqc_noalloc_scratch_bytes.argtypes = []
         L.tqc_noalloc_scratch_bytes.restype = ctypes.c_int64
+        fp, i32p = ctypes.POINTER(ctypes.c_float), ctypes.POINTER(i32)
+        L.tqc_costmodel_create.argtypes = [i32, ctypes.c_uint64, ctypes.POINTER(vp)]
+        L.tqc_costmodel_destroy.argtypes = [vp]
+        L.tqc_costmodel_params.argtypes = [vp, vp, i32p]
+        L.tqc_costmodel_set_params.argtypes = [vp, vp, i32]
+        L.tqc_costmodel_grad.argtypes = [vp, vp, vp, i32, vp, fp]
+        L.tqc_costmodel_train.argtypes = [vp, vp, vp, i32, i32, i32, ctypes.c_float, ctypes.c_uint64, fp]
+        L.tqc_costmodel_predict.argtypes = [vp, vp, i32, vp]
+        L.tqc_costmodel_save.argtypes = [vp, ctypes.c_char_p]
+        L.tqc_costmodel_load.argtypes = [ctypes.c_char_p, ctypes.POINTER(vp)]
+        L.tqc_plan_features.argtypes = [vp, vp, i32]
+        L.tqc_plan_candidates.argtypes = [vp, ctypes.POINTER(PlanOpts), i32, vp, i32p]
+        for name in ["tqc_costmodel_create", "tqc_costmodel_destroy", "tqc_costmodel_params",
+                     "tqc_costmodel_set_params", "tqc_costmodel_grad", "tqc_costmodel_train",
+                     "tqc_costmodel_predict", "tqc_costmodel_save", "tqc_costmodel_load", "tqc_plan_features",
+                     "tqc_plan_candidates"]:
+            getattr(L, name).restype = ctypes.c_int
         for name in ["tqc_network_create", "tqc_network_upload", "tqc_destroy", "tqc_plan", "tqc_plan_info",
                      "tqc_plan_step", "tqc_contract", "tqc_contract_host", "tqc_contract_batch",
                      "tqc_plan_destroy", "tqc_plan_profile", "tqc_plan_step_time"]:
@@ -269,6 +290,12 @@ class Plan:
                                           None if fb is None else fb.ctypes.data, out.data_ptr(), dt,
                                           _stream_ptr(stream)))
 
+    def features(self):
+        """The plan's TQC_PLAN_FEATURES cost-model features (float32)."""
+        f = np.zeros(PLAN_FEATURES, np.float32)
+        _check(lib().tqc_plan_features(self.handle, f.ctypes.data, PLAN_FEATURES))
+        return f
+
     def profile(self, enable=True):
         _check(lib().tqc_plan_profile(self.handle, int(enable)))
 
@@ -284,6 +311,89 @@ class Plan:
             self.handle = None
             if self in self.net.plans:
                 self.net.plans.remove(self)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def plan_candidates(net: Network, max_n=24, precision=PREC_AUTO, free_qubits=None):
+    """Candidate contraction orders (lists of (a, b) pairs) of a network."""
+    o = PlanOpts()
+    lib().tqc_plan_opts_default(ctypes.byref(o))
+    o.precision = PREC_NAMES[precision] if isinstance(precision, str) else precision
+    if free_qubits is not None:
+        o.use_free_mask = 1
+        o.free_mask_lo = sum(1 << q for q in free_qubits if q < 64)
+        o.free_mask_hi = sum(1 << (q - 64) for q in free_qubits if q >= 64)
+    per = 2 * (net.m - 1)
+    buf = np.zeros(max(1, max_n * per), np.int32)
+    n = ctypes.c_int32()
+    _check(lib().tqc_plan_candidates(net.handle, ctypes.byref(o), max_n, buf.ctypes.data, ctypes.byref(n)))
+    return [buf[i * per:(i + 1) * per].reshape(-1, 2).tolist() for i in range(n.value)]
+
+
+class CostModel:
+    """The learned cost model (include/tqc.h, tqc_costmodel_*)."""
+
+    def __init__(self, n_features=PLAN_FEATURES, seed=0, _handle=None):
+        if _handle is not None:
+            self.handle = _handle
+        else:
+            h = ctypes.c_void_p()
+            _check(lib().tqc_costmodel_create(n_features, seed, ctypes.byref(h)))
+            self.handle = h
+        self.n_features = n_features
+
+    @classmethod
+    def load(cls, path):
+        h = ctypes.c_void_p()
+        _check(lib().tqc_costmodel_load(path.encode(), ctypes.byref(h)))
+        return cls(_handle=h)
+
+    def save(self, path):
+        _check(lib().tqc_costmodel_save(self.handle, path.encode()))
+
+    def params(self):
+        n = ctypes.c_int32()
+        _check(lib().tqc_costmodel_params(self.handle, None, ctypes.byref(n)))
+        out = np.zeros(n.value, np.float32)
+        _check(lib().tqc_costmodel_params(self.handle, out.ctypes.data, ctypes.byref(n)))
+        return out
+
+    def set_params(self, theta):
+        th = np.ascontiguousarray(theta, np.float32)
+        _check(lib().tqc_costmodel_set_params(self.handle, th.ctypes.data, len(th)))
+
+    def grad(self, X, t):
+        X = np.ascontiguousarray(X, np.float32)
+        t = np.ascontiguousarray(t, np.float32)
+        g = np.zeros(len(self.params()), np.float32)
+        loss = ctypes.c_float()
+        _check(lib().tqc_costmodel_grad(self.handle, X.ctypes.data, t.ctypes.data, len(t), g.ctypes.data,
+                                        ctypes.byref(loss)))
+        return loss.value, g
+
+    def train(self, X, logt, epochs=200, batch=64, lr=1e-3, seed=0):
+        X = np.ascontiguousarray(X, np.float32)
+        y = np.ascontiguousarray(logt, np.float32)
+        loss = ctypes.c_float()
+        _check(lib().tqc_costmodel_train(self.handle, X.ctypes.data, y.ctypes.data, len(y), epochs, batch, lr, seed,
+                                         ctypes.byref(loss)))
+        return loss.value
+
+    def predict(self, X):
+        X = np.ascontiguousarray(X, np.float32)
+        out = np.zeros(len(X), np.float32)
+        _check(lib().tqc_costmodel_predict(self.handle, X.ctypes.data, len(X), out.ctypes.data))
+        return out
+
+    def close(self):
+        if self.handle:
+            _check(lib().tqc_costmodel_destroy(self.handle))
+            self.handle = None
 
     def __del__(self):
         try:

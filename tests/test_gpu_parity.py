@@ -313,3 +313,20 @@ def test_total_mass_tracks_uploads():
         check_fp32(out.cpu().numpy().astype(np.float64), oracle.recon_bin(net), z_or)
     p.close()
     h.close()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
+def test_autotuned_plan_matches(prec):
+    """The autotuner only changes tile shapes, never results."""
+    net = chain3(1300, 0) if prec == "bf16x3" else small_pp(750, n=16, m=4, cuts=7)
+    want = oracle.recon_bin(net)
+    got, z, d = run(net, precision=prec, autotune=1)
+    h = tqc.Network(net)
+    p = tqc.Plan(h, precision=prec, autotune=1)
+    out = torch.empty(p.out_elems, dtype=torch.float32, device="cuda")
+    p.contract(out)
+    d = p.describe()
+    assert d["tuned"] == 1
+    check_fp32(out.cpu().numpy().astype(np.float64), want)
+    p.close()
+    h.close()
