@@ -202,15 +202,29 @@ TQC_API tqc_status tqc_contract_host(tqc_plan_t plan, const void *const *host_te
                                      void *host_out, int32_t out_dtype, double *z_out, void *cuda_stream);
 
 /*
- * Many plans (independent networks of uneven sizes) in one persistent
- * launch.  d_outs[i] receives plan i's bin (FP32).  Plans must each have been
- * contracted once (workspace allocated).  The launch is stream-ordered and
- * contains no host synchronisation, so it can be captured in a CUDA graph.
- * Device-side waits are bounded; a wait that gives up makes the call return
- * TQC_ERR_TIMEOUT at the next synchronising call (tqc_batch_status).
+ * Many plans (independent networks of uneven sizes) in one persistent launch:
+ * one kernel drains a device work list of every plan's ingest chunks and
+ * step tiles (CUDA-core and tcgen05), each waiting, with a bounded wait, on
+ * the counters of the items that produce its operands.  d_outs[i] receives
+ * plan i's bin (FP32, renormalised with the plan's cached total mass).
+ * Requirements: every plan was contracted once since its tensors last
+ * changed, and none is sliced (TQC_ERR_UNSUPPORTED otherwise).  The first
+ * call with a given (plans, outputs) list builds and uploads the work list
+ * (allocates, synchronises); repeated calls with the same list only reset
+ * the counters and launch, so they can be captured in a CUDA graph.  Calls
+ * that overlap on the GPU share the work list and race.
  */
 TQC_API tqc_status tqc_contract_batch(const tqc_plan_t *plans, void *const *d_outs, int32_t n,
                                       void *cuda_stream);
+
+/* Synchronise `cuda_stream` and report the last batched launch:
+ * TQC_ERR_TIMEOUT if one of its bounded device waits gave up. */
+TQC_API tqc_status tqc_batch_status(void *cuda_stream);
+
+/* Fault-injection hook for tests: while enabled, batched launches carry one
+ * extra item that waits on a counter nothing increments, so its bounded wait
+ * must give up (about one second) and tqc_batch_status must report it. */
+TQC_API tqc_status tqc_batch_inject_stall(int32_t enable);
 
 /*
  * Per-step device timing (for roofline reporting).  enable = 1 makes every

@@ -302,11 +302,6 @@ tqc_status tqc_plan_candidates(tqc_net_t net, const tqc_plan_opts *opts, int32_t
     return TQC_OK;
 }
 
-tqc_status tqc_contract_batch(const tqc_plan_t *plans, void *const *d_outs, int32_t n, void *stream) {
-    if (!plans || !d_outs || n < 0) return fail(TQC_ERR_INVALID, "NULL argument");
-    (void)stream;
-    return fail(TQC_ERR_UNSUPPORTED, "batched launch not built yet");
-}
 
 tqc_status tqc_plan_profile(tqc_plan_t plan, int32_t enable) {
     if (!plan) return fail(TQC_ERR_INVALID, "NULL plan");

@@ -1,0 +1,650 @@
+// Batched persistent launch: many independent reconstructions (plans of
+// uneven sizes) drained by one persistent kernel from a device work list.
+//
+// Work items, in dependency levels: ingest chunks of every plan's leaf
+// operands, then the tiles of each pairwise step (CUDA-core 64 x 64 tiles or
+// tensor-core 128 x BN tiles).  Every item names at most two counters it
+// waits for (its operands' producers) and one it increments.  CTAs claim
+// items in list order with an atomic counter, so an item only ever waits for
+// items already claimed by running CTAs: no co-residency is needed, and the
+// launch is stream-ordered and capturable in a CUDA graph.  Every wait is
+// bounded (about one second); a wait that gives up raises an error word that
+// tqc_batch_status reports, and the remaining CTAs stop at their next item.
+//
+// The tensor-core tile here is synchronous per CTA (TMA load, tcgen05.mma,
+// commit, TMEM load, epilogue); two CTAs per SM overlap each other's phases.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "device_common.cuh"
+#include "launch.h"
+
+struct tqc_plan {
+    tqc::Plan p;
+};
+
+namespace tqc {
+namespace {
+
+constexpr int NT = 128;
+constexpr long long BWAIT = 2000000000ll;  // ~1 s at the boost clock
+constexpr int64_t CHUNK = 1 << 16;          // ingest elements per item
+
+enum ItemKind { IT_INGEST = 0, IT_STEP = 1, IT_STALL = 2 };
+
+struct alignas(128) BStep {
+    CUtensorMap maps[4];  // A, B, A lo, B lo (tensor-core steps)
+    StepArgs a;
+    int32_t klass, prec, bn, rowmajor, gmode, pitch;
+    int64_t col_tiles;
+    int32_t dep[2];
+    int64_t need[2];
+    int32_t done;
+};
+
+struct BIngest {
+    IngestArgs g;
+    int64_t lo, hi;
+    int32_t done;
+};
+
+struct BItem {
+    int32_t kind, idx;
+    int64_t tile;
+};
+
+// shared memory carve-up (after 1024-byte alignment)
+constexpr int SM_STAGE = 65536;   // A, B, A lo, B lo: 4 x 16 KB (128-byte rows, <= 128 rows)
+constexpr int SM_STG = 128 * 68 * 4 > 64 * 132 * 4 ? 128 * 68 * 4 : 64 * 132 * 4;
+constexpr int SM_MISC = 256;
+constexpr int SMEM = 1024 + SM_STAGE + SM_STG + SM_MISC;
+
+__device__ __forceinline__ uint32_t s_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void bmbar_init(uint64_t *bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(s_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool bmbar_try(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(s_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ bool bmbar_wait(uint64_t *bar, uint32_t parity) {
+    const long long t0 = clock64();
+    while (!bmbar_try(bar, parity))
+        if (clock64() - t0 > BWAIT) return false;
+    return true;
+}
+
+__device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Bounded wait for counter >= need (thread 0 only).
+__device__ bool wait_counter(const unsigned long long *c, unsigned long long need, const int *err) {
+    const long long t0 = clock64();
+    while (ld_acquire(c) < need) {
+        if (*(volatile const int *)err) return false;
+        if (clock64() - t0 > BWAIT) return false;
+        __nanosleep(200);
+    }
+    return true;
+}
+
+__device__ __forceinline__ void tc_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+    uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)(1024 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+
+__device__ __forceinline__ void mma_issue(int prec, uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    if (prec == TQC_PREC_TF32)
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+            "l"(a), "l"(b), "r"(idesc), "r"(acc));
+    else
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+            "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void tmem_load32(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ void ingest_range(const BIngest &it, int tid) {
+    const IngestArgs &g = it.g;
+    for (int64_t d = it.lo + tid; d < it.hi; d += NT) {
+        int64_t s = g.src_base;
+        for (int b = 0; b < g.nbits; ++b)
+            if (d >> b & 1) s += 1ll << g.srcpos[b];
+        const double v64 = g.src_dtype == TQC_F64 ? ((const double *)g.src)[s] : (double)((const float *)g.src)[s];
+        if (g.scaled) {
+            ((float *)g.dst)[d] = (float)(v64 * g.zinfo[1]);
+            continue;
+        }
+        const float v = (float)v64;
+        switch (g.storage) {
+            case ST_F32: ((float *)g.dst)[d] = v; break;
+            case ST_TF32: ((float *)g.dst)[d] = to_tf32(v); break;
+            case ST_BF16: ((__nv_bfloat16 *)g.dst)[d] = __float2bfloat16_rn(v); break;
+            case ST_BF16X2: {
+                __nv_bfloat16 h = __float2bfloat16_rn(v);
+                ((__nv_bfloat16 *)g.dst)[d] = h;
+                ((__nv_bfloat16 *)g.dst_lo)[d] = __float2bfloat16_rn((float)(v64 - (double)__bfloat162float(h)));
+            } break;
+            default: break;
+        }
+    }
+}
+
+// 64 x 64 CUDA-core tile: 128 threads, 4 x 8 results each.
+__device__ void simt_tile(const BStep &st, const EpiTables *tb, int64_t tile, uint8_t *stage, float *stg,
+                          uint64_t *base_slot, int tid) {
+    constexpr int BM = 64, BN = 64, TM = 4, TN = 8, BK = 16, PA = BM + 4, PB = BN + 4, PS = BN + 4;
+    const StepArgs &a = st.a;
+    const EpiParams &e = a.epi;
+    float *As = (float *)stage, *Bs = As + BK * PA;
+    const int Me = 1 << e.a_bits, Ne = 1 << e.b_bits;
+    const int64_t K = 1ll << a.kb;
+    const int lkc = a.kb < 4 ? a.kb : 4, kc = 1 << lkc;
+    const float *A = (const float *)a.A, *B = (const float *)a.B;
+    const int tx = tid % (BN / TN), ty = tid / (BN / TN);
+    const int64_t rt = tile / st.col_tiles, ct = tile - rt * st.col_tiles;
+    const int64_t r0 = rt << e.a_bits, c0 = ct << e.b_bits;
+    if (tid == 0) *base_slot = tile_base(e, (uint64_t)rt, (uint64_t)ct);
+    float acc[TM][TN];
+#pragma unroll
+    for (int u = 0; u < TM; ++u)
+#pragma unroll
+        for (int v = 0; v < TN; ++v) acc[u][v] = 0.f;
+    for (int64_t k0 = 0; k0 < K; k0 += kc) {
+        for (int idx = tid; idx < (BM << lkc); idx += NT) {
+            int i = idx >> lkc, kk = idx & (kc - 1);
+            As[kk * PA + i] = i < Me ? A[(r0 + i) * K + k0 + kk] : 0.f;
+        }
+        for (int idx = tid; idx < (BN << lkc); idx += NT) {
+            int j = idx >> lkc, kk = idx & (kc - 1);
+            Bs[kk * PB + j] = j < Ne ? B[(c0 + j) * K + k0 + kk] : 0.f;
+        }
+        __syncthreads();
+        for (int kk = 0; kk < kc; ++kk) {
+            float af[TM], bf[TN];
+#pragma unroll
+            for (int u = 0; u < TM; ++u) af[u] = As[kk * PA + ty * TM + u];
+#pragma unroll
+            for (int v = 0; v < TN; v += 4) *(float4 *)&bf[v] = *(const float4 *)&Bs[kk * PB + tx * TN + v];
+#pragma unroll
+            for (int u = 0; u < TM; ++u)
+#pragma unroll
+                for (int v = 0; v < TN; ++v) acc[u][v] = fmaf(af[u], bf[v], acc[u][v]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int u = 0; u < TM; ++u)
+#pragma unroll
+        for (int v = 0; v < TN; v += 4)
+            *(float4 *)&stg[(ty * TM + u) * PS + tx * TN + v] =
+                make_float4(acc[u][v], acc[u][v + 1], acc[u][v + 2], acc[u][v + 3]);
+    __syncthreads();
+    epi_readout(tb, stg, e, *base_slot, Me * Ne, tid, NT, st.gmode);
+}
+
+// 128 x bn tensor-core tile (synchronous: TMA, MMA, TMEM load, epilogue).
+__device__ bool umma_tile(const BStep &st, const EpiTables *tb, int64_t tile, uint8_t *stage, float *stg,
+                          uint64_t *bars, uint64_t *base_slot, uint32_t tmem, uint32_t &tph, uint32_t &mph,
+                          int *ok_slot, int tid) {
+    const StepArgs &a = st.a;
+    const EpiParams &e = a.epi;
+    const int warp = tid >> 5, lane = tid & 31;
+    const int64_t rt = tile / st.col_tiles, ct = tile - rt * st.col_tiles;
+    const int elem = st.prec == TQC_PREC_TF32 ? 4 : 2;
+    const int bk = 128 / elem;
+    const int kblocks = (int)((1ll << a.kb) / bk);
+    const bool x3 = st.prec == TQC_PREC_BF16X3;
+    const uint32_t idesc = (1u << 4) | ((st.prec == TQC_PREC_TF32 ? 2u : 1u) << 7) |
+                           ((st.prec == TQC_PREC_TF32 ? 2u : 1u) << 10) | ((uint32_t)(st.bn >> 3) << 17) |
+                           ((uint32_t)(128 >> 4) << 24);
+    if (tid == 0) {
+        bool ok = true;
+        asm volatile("fence.proxy.async.global;" ::: "memory");
+        const uint32_t bytes = (uint32_t)((128 + st.bn) * 128 * (x3 ? 2 : 1));
+        uint8_t *sA = stage, *sB = stage + 16384, *sAl = stage + 32768, *sBl = stage + 49152;
+        for (int kb = 0; kb < kblocks && ok; ++kb) {
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(s_u32(&bars[0])), "r"(bytes)
+                         : "memory");
+            const CUtensorMap *mp = st.maps;
+            const int c0 = kb * bk;
+            const int ra = (int)(rt * 128), rb = (int)(ct * st.bn);
+#define BT_LOAD(dst, map, y)                                                                                       \
+    asm volatile(                                                                                                  \
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"( \
+            s_u32(dst)),                                                                                           \
+        "l"((uint64_t)(map)), "r"(c0), "r"(y), "r"(s_u32(&bars[0]))                                                \
+        : "memory")
+            BT_LOAD(sA, &mp[0], ra);
+            BT_LOAD(sB, &mp[1], rb);
+            if (x3) {
+                BT_LOAD(sAl, &mp[2], ra);
+                BT_LOAD(sBl, &mp[3], rb);
+            }
+#undef BT_LOAD
+            ok = bmbar_wait(&bars[0], tph);
+            tph ^= 1u;
+            if (!ok) break;
+            tc_after();
+            const uint32_t a0 = s_u32(sA), b0 = s_u32(sB), al = s_u32(sAl), bl = s_u32(sBl);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const uint64_t da = sw128_desc(a0 + 32 * k), db = sw128_desc(b0 + 32 * k);
+                mma_issue(st.prec, tmem, da, db, idesc, (kb | k) != 0);
+                if (x3) {
+                    mma_issue(st.prec, tmem, da, sw128_desc(bl + 32 * k), idesc, 1u);
+                    mma_issue(st.prec, tmem, sw128_desc(al + 32 * k), db, idesc, 1u);
+                }
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             s_u32(&bars[1]))
+                         : "memory");
+            ok = bmbar_wait(&bars[1], mph);  // the stage is reused by the next k-block
+            mph ^= 1u;
+        }
+        *ok_slot = ok ? 1 : 0;
+    }
+    tc_before();
+    __syncthreads();
+    tc_after();
+    if (!*ok_slot) return false;
+    const int subs = st.bn / 64;
+    const int Me = 1 << e.a_bits, Ne = 1 << e.b_bits;
+    const int row = warp * 32 + lane;
+    for (int h = 0; h < subs; ++h) {
+        if (tid == 0) *base_slot = tile_base(e, (uint64_t)rt, (uint64_t)(ct * subs + h));
+        for (int c = 0; c < 2; ++c) {
+            uint32_t r[32];
+            tmem_load32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(h * 64 + c * 32), r);
+            if (row < Me) {
+                if (st.rowmajor) {
+#pragma unroll
+                    for (int j = 0; j < 32; j += 4)
+                        if (c * 32 + j < Ne)
+                            *(float4 *)(stg + row * st.pitch + c * 32 + j) =
+                                make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]), __uint_as_float(r[j + 2]),
+                                            __uint_as_float(r[j + 3]));
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j)
+                        if (c * 32 + j < Ne) stg[(c * 32 + j) * st.pitch + row] = __uint_as_float(r[j]);
+                }
+            }
+        }
+        __syncthreads();
+        epi_readout(tb, stg, e, *base_slot, Me * Ne, tid, NT, st.gmode);
+        __syncthreads();
+    }
+    tc_before();
+    return true;
+}
+
+__global__ void __launch_bounds__(NT, 2)
+    batch_kernel(const BItem *items, int64_t n_items, const BStep *steps, const EpiTables *tables, const BIngest *ing,
+                 unsigned long long *counters, unsigned long long *next, int *err) {
+    extern __shared__ uint8_t raw[];
+    uint8_t *sm = (uint8_t *)(((uintptr_t)raw + 1023) & ~(uintptr_t)1023);
+    uint8_t *stage = sm;
+    float *stg = (float *)(sm + SM_STAGE);
+    uint64_t *bars = (uint64_t *)(sm + SM_STAGE + SM_STG);  // [0] TMA, [1] MMA
+    uint32_t *tmem_slot = (uint32_t *)(bars + 2);
+    int64_t *item_slot = (int64_t *)(bars + 3);
+    uint64_t *base_slot = (uint64_t *)(bars + 4);
+    int *ok_slot = (int *)(bars + 5);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    if (tid == 0) {
+        bmbar_init(&bars[0]);
+        bmbar_init(&bars[1]);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;" ::"r"(s_u32(tmem_slot))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_before();
+    __syncthreads();
+    tc_after();
+    const uint32_t tmem = *tmem_slot;
+    uint32_t tph = 0, mph = 0;
+    for (;;) {
+        if (tid == 0) *item_slot = *(volatile int *)err ? n_items : (int64_t)atomicAdd(next, 1ull);
+        __syncthreads();
+        const int64_t it = *item_slot;
+        __syncthreads();
+        if (it >= n_items) break;
+        const BItem item = items[it];
+        if (item.kind == IT_INGEST) {
+            const BIngest &g = ing[item.idx];
+            ingest_range(g, tid);
+            __threadfence();
+            __syncthreads();
+            if (tid == 0) atomicAdd(&counters[g.done], 1ull);
+            continue;
+        }
+        if (tid == 0) {
+            bool ok = true;
+            if (item.kind == IT_STALL) {
+                ok = wait_counter(&counters[item.idx], 1ull, err);  // nothing increments it
+            } else {
+                const BStep &st = steps[item.idx];
+                for (int d = 0; d < 2 && ok; ++d)
+                    if (st.dep[d] >= 0) ok = wait_counter(&counters[st.dep[d]], (unsigned long long)st.need[d], err);
+            }
+            if (!ok) atomicExch(err, 1);
+            *ok_slot = ok ? 1 : 0;
+        }
+        __syncthreads();
+        if (!*ok_slot || item.kind == IT_STALL) continue;
+        const BStep &st = steps[item.idx];
+        bool ok = true;
+        if (st.klass == KC_UMMA)
+            ok = umma_tile(st, &tables[item.idx], item.tile, stage, stg, bars, base_slot, tmem, tph, mph, ok_slot, tid);
+        else
+            simt_tile(st, &tables[item.idx], item.tile, stage, stg, base_slot, tid);
+        __threadfence();
+        __syncthreads();
+        if (tid == 0) {
+            if (ok) atomicAdd(&counters[st.done], 1ull);
+            else atomicExch(err, 1);
+        }
+    }
+    __syncthreads();
+    if (warp == 0) {
+        tc_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(tmem) : "memory");
+    }
+}
+
+// ------------------------------------------------------------------ host side
+uint64_t h_pdep(uint64_t src, uint64_t mask) {
+    uint64_t r = 0;
+    while (mask) {
+        uint64_t low = mask & (~mask + 1);
+        if (src & 1) r |= low;
+        src >>= 1;
+        mask ^= low;
+    }
+    return r;
+}
+uint32_t h_pext(uint32_t x, uint32_t mask) {
+    uint32_t r = 0, k = 0;
+    while (mask) {
+        uint32_t low = mask & (~mask + 1);
+        if (x & low) r |= 1u << k;
+        ++k;
+        mask ^= low;
+    }
+    return r;
+}
+
+void host_tables(EpiTables *tb, const EpiParams &e, bool rowmajor, int pitch) {
+    for (int u = 0; u < 384; ++u) {
+        const bool lo = u < 128;
+        const uint32_t t = lo ? (uint32_t)u : (uint32_t)(u - 128) << 7;
+        const uint32_t i = h_pext(t, e.lowRc), j = h_pext(t, e.lowCc);
+        const uint32_t s = rowmajor ? i * pitch + j : j * pitch + i;
+        const uint64_t g = h_pdep(t, e.tileMask);
+        if (lo) {
+            tb->s_lo[u] = s;
+            tb->g_lo[u] = g;
+        } else {
+            tb->s_hi[u - 128] = s;
+            tb->g_hi[u - 128] = g;
+        }
+    }
+}
+
+struct Batch {
+    std::vector<const void *> key;
+    BItem *d_items = nullptr;
+    BStep *d_steps = nullptr;
+    EpiTables *d_tables = nullptr;
+    BIngest *d_ing = nullptr;
+    unsigned long long *d_counters = nullptr;  // [counters..., next]
+    int *d_err = nullptr;
+    int64_t n_items = 0, n_counters = 0;
+    void release() {
+        cudaFree(d_items);
+        cudaFree(d_steps);
+        cudaFree(d_tables);
+        cudaFree(d_ing);
+        cudaFree(d_counters);
+        cudaFree(d_err);
+        *this = Batch();
+    }
+};
+
+std::mutex g_batch_mu;
+Batch g_batch;
+int g_inject_stall = 0;
+
+template <typename T>
+cudaError_t upload(T **dst, const std::vector<T> &v) {
+    if (v.empty()) {
+        *dst = nullptr;
+        return cudaSuccess;
+    }
+    cudaError_t e = cudaMalloc((void **)dst, sizeof(T) * v.size());
+    if (e != cudaSuccess) return e;
+    return cudaMemcpy(*dst, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice);
+}
+
+tqc_status build_batch(Plan *const *plans, void *const *outs, int n, Batch *b) {
+    std::vector<BItem> items;
+    std::vector<BStep> steps;
+    std::vector<EpiTables> tables;
+    std::vector<BIngest> ing;
+    std::vector<int> step_level;
+    std::vector<std::pair<int, BItem>> leveled;  // (level, item)
+    int n_counters = 0;
+    for (int pi = 0; pi < n; ++pi) {
+        Plan &p = *plans[pi];
+        if (!p.ready) return fail(TQC_ERR_INVALID, "batch: plan " + std::to_string(pi) + " was never contracted");
+        if (p.n_slices() > 1) return fail(TQC_ERR_UNSUPPORTED, "batch: plan " + std::to_string(pi) + " is sliced");
+        if (p.z_version != p.net->version)
+            return fail(TQC_ERR_INVALID, "batch: plan " + std::to_string(pi) + " has changed tensors; contract it once");
+        // ingest chunks (all leaves of the plan count on one counter)
+        const int ing_counter = n_counters++;
+        int64_t n_chunks = 0;
+        for (int j = 0; j < p.m; ++j) {
+            const TensorPlan &t = p.tensors[j];
+            BIngest bi;
+            bi.g = exec_leaf_args(p, t, j, p.fixed_bits.data());
+            if (p.m == 1) {
+                bi.g.dst = outs[pi];
+                bi.g.scaled = 1;
+                bi.g.zinfo = p.d_zinfo;
+            } else {
+                bi.g.dst = (char *)p.d_ws + t.offset;
+                if (t.storage == ST_BF16X2) bi.g.dst_lo = (char *)p.d_ws + t.offset + t.plane_bytes;
+                bi.g.storage = t.storage;
+            }
+            bi.done = ing_counter;
+            const int64_t total = p.m == 1 ? p.out_elems() : ((int64_t)1 << t.nbits());
+            for (int64_t lo = 0; lo < total; lo += CHUNK) {
+                bi.lo = lo;
+                bi.hi = std::min(total, lo + CHUNK);
+                leveled.push_back({0, BItem{IT_INGEST, (int)ing.size(), 0}});
+                ing.push_back(bi);
+                ++n_chunks;
+            }
+        }
+        // steps
+        std::vector<int> counter_of(p.tensors.size(), -1), level_of(p.tensors.size(), 0);
+        std::vector<int64_t> tiles_of(p.tensors.size(), 0);
+        for (int j = 0; j < p.m; ++j) {
+            counter_of[j] = ing_counter;
+            tiles_of[j] = n_chunks;
+        }
+        for (const StepPlan &sp : p.steps) {
+            BStep bs;
+            std::memset((void *)&bs, 0, sizeof bs);
+            bs.klass = sp.klass;
+            bs.prec = sp.prec;
+            TileShape ts = sp.klass == KC_UMMA ? TileShape{7, 6} : TileShape{6, 6};
+            bs.a = exec_step_args(p, sp, ts);
+            const TensorPlan &tc = p.tensors[sp.c];
+            bs.a.epi.zinfo = p.d_zinfo;
+            if (sp.final) {
+                bs.a.epi.out = outs[pi];
+                bs.a.epi.mode = EPI_OUT_F32;
+            } else {
+                bs.a.epi.out = (char *)p.d_ws + tc.offset;
+                if (tc.storage == ST_BF16X2) bs.a.epi.out_lo = (char *)p.d_ws + tc.offset + tc.plane_bytes;
+                bs.a.epi.mode = exec_epi_mode(tc.storage);
+            }
+            int64_t row_tiles = (int64_t)1 << (sp.mb - bs.a.epi.a_bits);
+            if (sp.klass == KC_UMMA) {
+                bs.bn = sp.nb >= 7 ? 128 : 64;
+                const int lbn = bs.bn == 128 ? 7 : 6;
+                bs.col_tiles = sp.nb >= lbn ? (int64_t)1 << (sp.nb - lbn) : 1;
+                StagePick pk = pick_staging(bs.a.epi.lowRc, bs.a.epi.lowCc);
+                bs.rowmajor = pk.rowmajor;
+                bs.gmode = pk.gmode;
+                bs.pitch = pk.rowmajor ? 68 : 132;
+                if (umma_make_maps(sp.prec, bs.a, bs.bn, bs.maps) != cudaSuccess)
+                    return fail(TQC_ERR_CUDA, "batch: tensor map of plan " + std::to_string(pi));
+            } else {
+                bs.bn = 64;
+                bs.col_tiles = (int64_t)1 << (sp.nb - bs.a.epi.b_bits);
+                bs.rowmajor = 1;
+                bs.gmode = gather_mode(bs.a.epi.lowCc);
+                bs.pitch = 68;
+            }
+            const int64_t n_tiles = row_tiles * bs.col_tiles;
+            bs.dep[0] = counter_of[sp.a];
+            bs.need[0] = tiles_of[sp.a];
+            bs.dep[1] = counter_of[sp.b];
+            bs.need[1] = tiles_of[sp.b];
+            if (bs.dep[1] == bs.dep[0]) bs.dep[1] = -1;
+            bs.done = n_counters++;
+            counter_of[sp.c] = bs.done;
+            tiles_of[sp.c] = n_tiles;
+            const int lvl = 1 + std::max(level_of[sp.a], level_of[sp.b]);
+            level_of[sp.c] = lvl;
+            EpiTables tb;
+            host_tables(&tb, bs.a.epi, bs.rowmajor != 0, bs.pitch);
+            const int si = (int)steps.size();
+            steps.push_back(bs);
+            tables.push_back(tb);
+            for (int64_t t = 0; t < n_tiles; ++t) leveled.push_back({lvl, BItem{IT_STEP, si, t}});
+        }
+    }
+    if (g_inject_stall) leveled.insert(leveled.begin(), {0, BItem{IT_STALL, n_counters++, 0}});
+    std::stable_sort(leveled.begin(), leveled.end(), [](auto &x, auto &y) { return x.first < y.first; });
+    for (auto &li : leveled) items.push_back(li.second);
+    b->n_items = (int64_t)items.size();
+    b->n_counters = n_counters;
+    cudaError_t e = upload(&b->d_items, items);
+    if (e == cudaSuccess) e = upload(&b->d_steps, steps);
+    if (e == cudaSuccess) e = upload(&b->d_tables, tables);
+    if (e == cudaSuccess) e = upload(&b->d_ing, ing);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_counters, sizeof(unsigned long long) * (n_counters + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(b->d_err, 0, sizeof(int));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        b->release();
+        return fail(TQC_ERR_OOM, std::string("batch set-up: ") + cudaGetErrorString(e));
+    }
+    return TQC_OK;
+}
+
+}  // namespace
+}  // namespace tqc
+
+using namespace tqc;
+
+extern "C" {
+
+tqc_status tqc_contract_batch(const tqc_plan_t *plans, void *const *d_outs, int32_t n, void *cuda_stream) {
+    if (!plans || !d_outs || n < 1) return fail(TQC_ERR_INVALID, "bad batch arguments");
+    for (int i = 0; i < n; ++i)
+        if (!plans[i] || !d_outs[i]) return fail(TQC_ERR_INVALID, "NULL plan or output in batch");
+    std::lock_guard<std::mutex> lk(g_batch_mu);
+    std::vector<const void *> key;
+    for (int i = 0; i < n; ++i) {
+        key.push_back(plans[i]);
+        key.push_back(d_outs[i]);
+    }
+    key.push_back((const void *)(intptr_t)g_inject_stall);
+    if (key != g_batch.key) {
+        g_batch.release();
+        std::vector<Plan *> ps;
+        for (int i = 0; i < n; ++i) ps.push_back(&plans[i]->p);
+        tqc_status st = build_batch(ps.data(), d_outs, n, &g_batch);
+        if (st != TQC_OK) return st;
+        g_batch.key = key;
+        static bool attr = false;
+        if (!attr) {
+            if (cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM) != cudaSuccess)
+                return fail(TQC_ERR_CUDA, "batch kernel attributes");
+            attr = true;
+        }
+    }
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    cudaError_t e = cudaMemsetAsync(g_batch.d_counters, 0, sizeof(unsigned long long) * (g_batch.n_counters + 1), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(g_batch.d_err, 0, sizeof(int), s);
+    if (e != cudaSuccess) return fail(TQC_ERR_CUDA, std::string("batch reset: ") + cudaGetErrorString(e));
+    const int grid = 2 * sm_count();
+    batch_kernel<<<grid, NT, SMEM, s>>>(g_batch.d_items, g_batch.n_items, g_batch.d_steps, g_batch.d_tables,
+                                        g_batch.d_ing, g_batch.d_counters, g_batch.d_counters + g_batch.n_counters,
+                                        g_batch.d_err);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(TQC_ERR_CUDA, std::string("batch launch: ") + cudaGetErrorString(e));
+    return TQC_OK;
+}
+
+tqc_status tqc_batch_status(void *cuda_stream) {
+    std::lock_guard<std::mutex> lk(g_batch_mu);
+    if (!g_batch.d_err) return fail(TQC_ERR_INVALID, "no batch launched");
+    int h = 0;
+    cudaError_t e = cudaMemcpyAsync(&h, g_batch.d_err, sizeof(int), cudaMemcpyDeviceToHost, (cudaStream_t)cuda_stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)cuda_stream);
+    if (e != cudaSuccess) return fail(TQC_ERR_CUDA, std::string("batch status: ") + cudaGetErrorString(e));
+    if (h) return fail(TQC_ERR_TIMEOUT, "a bounded wait in the batched launch gave up");
+    return TQC_OK;
+}
+
+tqc_status tqc_batch_inject_stall(int32_t enable) {
+    std::lock_guard<std::mutex> lk(g_batch_mu);
+    g_inject_stall = enable ? 1 : 0;
+    return TQC_OK;
+}
+
+}  // extern "C"

@@ -157,6 +157,14 @@ std::vector<int> tile_candidates(const StepPlan &st) {
 
 }  // namespace
 
+IngestArgs exec_leaf_args(const Plan &p, const TensorPlan &t, int j, const uint8_t *fixed) {
+    return leaf_args(p, t, j, fixed, 0, false);
+}
+StepArgs exec_step_args(const Plan &p, const StepPlan &st, TileShape tile) {
+    return step_args(p, p.tensors, st, p.d_ws, tile);
+}
+int exec_epi_mode(int storage) { return epi_mode_of(storage); }
+
 tqc_status exec_autotune(Plan *p, void *d_out, int out_dtype, cudaStream_t s) {
     const bool sliced = p->n_slices() > 1;
     cudaEvent_t e0, e1;

@@ -30,6 +30,12 @@ enum UmmaCfg { UMMA_128x128 = 0, UMMA_128x64 = 1, UMMA_N_CFG = 2 };
 TileShape umma_tile(int cfg);
 // prec: TQC_PREC_BF16 / TQC_PREC_BF16X3 / TQC_PREC_TF32
 cudaError_t launch_umma_step(int cfg, int prec, const StepArgs &a, int *d_err, cudaStream_t s);
+cudaError_t umma_make_maps(int prec, const StepArgs &a, int bn, void *maps_out);  // 4 CUtensorMap
+
+// Argument blocks the executor builds (executor.cu), reused by the batched launch.
+IngestArgs exec_leaf_args(const Plan &p, const TensorPlan &t, int j, const uint8_t *fixed);
+StepArgs exec_step_args(const Plan &p, const StepPlan &st, TileShape tile);
+int exec_epi_mode(int storage);
 
 // Epilogue parameters for a step given its result masks and tile shape.
 EpiParams make_epi(uint64_t maskR, uint64_t maskC, int mb, int nb, TileShape t);

@@ -546,6 +546,28 @@ cudaError_t launch_bn(int prec, const StepArgs &a, int *d_err, cudaStream_t s) {
 
 }  // namespace
 
+// Tensor maps of a step's operands for a 128 x bn MMA tile (the batched
+// launch builds them once at set-up): maps[0..3] = A, B, A lo, B lo.
+cudaError_t umma_make_maps(int prec, const StepArgs &a, int bn, void *maps_out) {
+    cudaError_t e = get_encode();
+    if (e != cudaSuccess) return e;
+    CUtensorMap *m = (CUtensorMap *)maps_out;
+    const int elem = prec == TQC_PREC_TF32 ? 4 : 2;
+    const uint32_t bk = 128 / elem;
+    const uint64_t M = 1ull << a.mb, N = 1ull << a.nb, K = 1ull << a.kb;
+    if (K < bk) return cudaErrorInvalidValue;
+    if ((e = encode(&m[0], a.A, elem, K, M, bk, BM)) != cudaSuccess) return e;
+    if ((e = encode(&m[1], a.B, elem, K, N, bk, (uint32_t)bn)) != cudaSuccess) return e;
+    if (prec == TQC_PREC_BF16X3) {
+        if ((e = encode(&m[2], a.A_lo, elem, K, M, bk, BM)) != cudaSuccess) return e;
+        if ((e = encode(&m[3], a.B_lo, elem, K, N, bk, (uint32_t)bn)) != cudaSuccess) return e;
+    } else {
+        m[2] = m[0];
+        m[3] = m[1];
+    }
+    return cudaSuccess;
+}
+
 // Epilogue tile of both configurations (the MMA tile is 128 x 128 or 128 x 64).
 TileShape umma_tile(int cfg) {
     (void)cfg;

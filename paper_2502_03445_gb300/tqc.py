@@ -32,7 +32,7 @@ EXPORTS = ["tqc_network_create", "tqc_network_upload", "tqc_destroy", "tqc_plan_
            "tqc_contract_noalloc", "tqc_noalloc_scratch_bytes", "tqc_costmodel_create", "tqc_costmodel_destroy",
            "tqc_costmodel_params", "tqc_costmodel_set_params", "tqc_costmodel_grad", "tqc_costmodel_train",
            "tqc_costmodel_predict", "tqc_costmodel_save", "tqc_costmodel_load", "tqc_plan_features",
-           "tqc_plan_candidates"]
+           "tqc_plan_candidates", "tqc_batch_status", "tqc_batch_inject_stall"]
 PLAN_FEATURES = 32
 
 
@@ -102,7 +102,10 @@ def lib():
         L.tqc_costmodel_load.argtypes = [ctypes.c_char_p, ctypes.POINTER(vp)]
         L.tqc_plan_features.argtypes = [vp, vp, i32]
         L.tqc_plan_candidates.argtypes = [vp, ctypes.POINTER(PlanOpts), i32, vp, i32p]
-        for name in ["tqc_costmodel_create", "tqc_costmodel_destroy", "tqc_costmodel_params",
+        L.tqc_batch_status.argtypes = [vp]
+        L.tqc_batch_inject_stall.argtypes = [i32]
+        for name in ["tqc_batch_status", "tqc_batch_inject_stall", "tqc_costmodel_create", "tqc_costmodel_destroy",
+                     "tqc_costmodel_params",
                      "tqc_costmodel_set_params", "tqc_costmodel_grad", "tqc_costmodel_train",
                      "tqc_costmodel_predict", "tqc_costmodel_save", "tqc_costmodel_load", "tqc_plan_features",
                      "tqc_plan_candidates"]:
@@ -408,3 +411,14 @@ def contract_batch(plans, outs, stream=None):
     ho = (ctypes.c_void_p * n)(*[o.data_ptr() for o in outs])
     _check(lib().tqc_contract_batch(ctypes.cast(hp, ctypes.c_void_p), ctypes.cast(ho, ctypes.c_void_p), n,
                                     _stream_ptr(stream)))
+
+
+def batch_status(stream=None):
+    """Synchronise and raise TqcError(ERR_TIMEOUT) if the last batched
+    launch had a bounded wait give up."""
+    _check(lib().tqc_batch_status(_stream_ptr(stream)))
+
+
+def batch_inject_stall(enable: bool):
+    """Fault-injection hook: batched launches carry an item whose wait can never be met."""
+    _check(lib().tqc_batch_inject_stall(int(enable)))

@@ -1,0 +1,111 @@
+"""Batched persistent launch: many plans of uneven sizes in one kernel, under
+a captured CUDA graph, with bounded device waits."""
+import numpy as np
+import pytest
+
+import oracle
+from gen import Network, Node, tensors
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2502_03445_gb300 import tqc  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.set_device(0)
+
+
+def uneven_networks():
+    nets = [tensors.shape_matched_network(12 + k, 2 + k % 4, 3 + k, 12 if k == 4 else 9, seed=3000 + k)
+            for k in range(6)]
+    outs = [[0, 3, 6, 9, 12, 15], [1, 4, 7, 10, 13], [2, 5, 8, 11, 14]]
+    nets.append(tensors.pseudo_physical_network(16, [(0, 1)] * 3 + [(1, 2)] * 3, outs, 3100))  # tensor-core steps
+    rng = np.random.Generator(np.random.PCG64(5))
+    nets.append(Network(5, 0, [Node([4, 0, 2, 1, 3], [], [], rng.random(32))]))                # one subcircuit
+    return nets
+
+
+def prepared(nets, precs):
+    hs, plans, outs, want = [], [], [], []
+    for net, prec in zip(nets, precs):
+        h = tqc.Network(net)
+        p = tqc.Plan(h, precision=prec)
+        o = torch.empty(p.out_elems, dtype=torch.float32, device="cuda")
+        z = p.contract(o, want_z=True)        # allocates the workspace and caches Z
+        hs.append(h)
+        plans.append(p)
+        outs.append(torch.full_like(o, float("nan")))
+        want.append(oracle.recon_bin(net) / oracle.total_mass(net))
+    return hs, plans, outs, want
+
+
+def check(outs, want, tol):
+    for o, w in zip(outs, want):
+        got = o.cpu().numpy().astype(np.float64)
+        err = np.abs(got - w).max()
+        assert err <= tol * max(np.abs(w).max(), 1e-30), err
+
+
+@pytest.mark.parametrize("mode", ["fp32", "auto", "mixed"])
+def test_batch_matches_oracle(mode):
+    nets = uneven_networks()
+    precs = {"fp32": ["fp32"] * len(nets), "auto": ["auto"] * len(nets),
+             "mixed": ["fp32", "bf16x3", "tf32", "auto", "fp32", "bf16x3", "tf32", "fp32"]}[mode]
+    hs, plans, outs, want = prepared(nets, precs)
+    tqc.contract_batch(plans, outs)
+    tqc.batch_status()
+    check(outs, want, 1e-4 if mode != "mixed" else 2e-3)
+    for p in plans:
+        p.close()
+
+
+def test_batch_under_cuda_graph():
+    nets = uneven_networks()
+    hs, plans, outs, want = prepared(nets, ["auto"] * len(nets))
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        tqc.contract_batch(plans, outs, stream=s)   # first call builds the work list
+    s.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        tqc.contract_batch(plans, outs, stream=s)
+    for o in outs:
+        o.fill_(float("nan"))
+    for _ in range(2):
+        g.replay()
+    torch.cuda.synchronize()
+    tqc.batch_status()
+    check(outs, want, 1e-4)
+
+
+def test_batch_bounded_wait_reports_timeout():
+    """A wait that nothing can satisfy gives up after about a second; the
+    error is reported and the context stays usable."""
+    nets = uneven_networks()[:3]
+    hs, plans, outs, want = prepared(nets, ["fp32"] * 3)
+    tqc.batch_inject_stall(True)
+    try:
+        tqc.contract_batch(plans, outs)
+        with pytest.raises(tqc.TqcError) as ei:
+            tqc.batch_status()
+        assert ei.value.status == tqc.ERR_TIMEOUT
+    finally:
+        tqc.batch_inject_stall(False)
+    tqc.contract_batch(plans, outs)
+    tqc.batch_status()
+    check(outs, want, 1e-4)
+
+
+def test_batch_rejects_sliced_plans():
+    net = tensors.shape_matched_network(12, 3, 5, 9, seed=3200)
+    h = tqc.Network(net)
+    p = tqc.Plan(h, precision="fp32", sliced=[1])
+    o = torch.empty(p.out_elems, dtype=torch.float32, device="cuda")
+    p.contract(o)
+    with pytest.raises(tqc.TqcError) as ei:
+        tqc.contract_batch([p], [o])
+    assert ei.value.status == tqc.ERR_UNSUPPORTED
