@@ -48,6 +48,10 @@ def parse():
     ap.add_argument("--free-qubits", type=int, default=30,
                     help="reconstruct the bin of the lowest N qubits (others fixed to 0); 30 = full output")
     ap.add_argument("--no-clocks", action="store_true", help="skip the clock sampler and its load loop")
+    ap.add_argument("--batch", type=int, default=0,
+                    help="instead: time the batched persistent launch over this many networks")
+    ap.add_argument("--batch-n-lo", type=int, default=16)
+    ap.add_argument("--batch-n-hi", type=int, default=24)
     return ap.parse_args()
 
 
@@ -195,6 +199,100 @@ def run_reference(args):
     return 0
 
 
+def batch_networks(count, n_lo, n_hi, seed0=3000, max_node_elems=1 << 24):
+    """The batched workload's recipe: n ~ U{n_lo..n_hi}, m ~ U{2..8},
+    |E| ~ U{max(2, m-1)..12}, widths up to n; networks whose largest
+    subcircuit tensor exceeds max_node_elems are redrawn (count returned)."""
+    from gen import tensors
+    rng = np.random.Generator(np.random.PCG64(seed0))
+    nets, redraws = [], 0
+    while len(nets) < count:
+        n = int(rng.integers(n_lo, n_hi + 1))
+        m = int(rng.integers(2, 9))
+        cuts = int(rng.integers(max(2, m - 1), 13))
+        seed = int(rng.integers(1 << 30))
+        try:
+            shape_rng = np.random.Generator(np.random.PCG64(seed))
+            edges, outs = tensors.sample_shape(n, m, cuts, n, shape_rng, max_node_cuts=10)
+        except RuntimeError:
+            redraws += 1
+            continue
+        deg = [0] * m
+        for a, b in edges:
+            deg[a] += 1
+            deg[b] += 1
+        if max((4 ** deg[j]) << len(outs[j]) for j in range(m)) > max_node_elems:
+            redraws += 1
+            continue
+        nets.append(tensors.random_shape_network(n, m, cuts, n, seed, max_node_cuts=10))
+    return nets, redraws
+
+
+def run_batch(args):
+    """Batched persistent launch: `--batch` independent networks of uneven
+    sizes reconstructed by one tqc_contract_batch launch replayed from a CUDA
+    graph, against contracting them one after the other."""
+    import torch
+    from paper_2502_03445_gb300 import tqc
+    torch.cuda.set_device(0)
+    nets, redraws = batch_networks(args.batch, args.batch_n_lo, args.batch_n_hi)
+    hs, plans, outs = [], [], []
+    for net in nets:
+        h = tqc.Network(net, dtype=tqc.F32)
+        p = tqc.Plan(h, precision=args.precision)
+        o = torch.empty(p.out_elems, dtype=torch.float32, device="cuda")
+        p.contract(o)
+        hs.append(h)
+        plans.append(p)
+        outs.append(o)
+    units = sum(o.numel() for o in outs)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        tqc.contract_batch(plans, outs, stream=s)
+    s.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        tqc.contract_batch(plans, outs, stream=s)
+    for _ in range(args.warmup):
+        g.replay()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        g.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    tqc.batch_status()
+    ms = e0.elapsed_time(e1) / args.steps
+    # the same work as separate tqc_contract calls
+    for _ in range(2):
+        for p, o in zip(plans, outs):
+            p.contract(o)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(max(1, args.steps // 2)):
+        for p, o in zip(plans, outs):
+            p.contract(o)
+    e1.record()
+    torch.cuda.synchronize()
+    ms_seq = e0.elapsed_time(e1) / max(1, args.steps // 2)
+    classes = {}
+    for p in plans:
+        for st in p.describe()["steps"]:
+            classes[st["class"]] = classes.get(st["class"], 0) + 1
+    line = {"metric": METRIC, "value": units / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": args.precision, "data": "synthetic (Gaussian tensors, timing only)",
+            "config": {"workload": f"batch: {len(nets)} networks, n ~ U{{{args.batch_n_lo}..{args.batch_n_hi}}}, "
+                                   f"m ~ U{{2..8}}, |E| ~ U{{max(2,m-1)..12}}, full 2^n outputs, one persistent "
+                                   f"launch replayed from a CUDA graph",
+                       "outputs": units, "redraws": redraws, "step_classes": classes},
+            "sequential_contracts": {"ms_per_step": ms_seq, "value": units / (ms_seq / 1e3),
+                                     "speedup_of_batched": ms_seq / ms}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def time_plan(torch, plan, out, steps, warmup, profile=False):
     for _ in range(warmup):
         plan.contract(out)
@@ -214,6 +312,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.batch > 0:
+        return run_batch(args)
     ws, rank, local = dist_env()
     import torch
     import torch.distributed as dist
@@ -222,7 +322,7 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
     from gen import workloads
-    from paper_2502_03445_gb300 import tqc
+    from paper_2502_03445_gb300 import shard, tqc
 
     net = workloads.grid30(rank)          # weak scaling: one independent network per rank
     h = tqc.Network(net)
@@ -255,11 +355,10 @@ def main():
         dist.barrier()
     ms = s.elapsed_time(e) / args.steps
     clocks = sampler.stop() if sampler else None
-    if ws > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = probs_per_step * ws / (ms / 1e3)
+    # whole job: probabilities of every rank over the slowest rank's time
+    total_probs, sec = shard.aggregate(float(probs_per_step), ms / 1e3, dist if ws > 1 else None, "cuda")
+    ms = sec * 1e3
+    value = total_probs / sec
 
     # dominant kernel: the step with the largest mean duration over the timed region
     hbm, bf16, bf16_sus, peak_kind = peaks()
@@ -334,11 +433,8 @@ def main():
         for _ in range(args.e2e_steps):
             plan.contract_host(hin, hout)
         t_e2e = (time.perf_counter() - t0) / args.e2e_steps
-        if ws > 1:
-            t = torch.tensor([t_e2e], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            t_e2e = float(t.item())
-        line["e2e"] = {"value": probs_per_step * ws / t_e2e, "unit": UNIT,
+        e2e_probs, t_e2e = shard.aggregate(float(probs_per_step), t_e2e, dist if ws > 1 else None, "cuda")
+        line["e2e"] = {"value": e2e_probs / t_e2e, "unit": UNIT,
                        "h2d_bytes_per_step": int(sum(x.numel() * 8 for x in hin)),
                        "d2h_bytes_per_step": int(hout.numel() * 4), "ms_per_step": 1e3 * t_e2e}
     if rank == 0:
