@@ -112,9 +112,12 @@ def exact_network(cc: CutCircuit) -> Network:
     return net
 
 
-def pseudo_physical_tensor(cut_role, n_out: int, rng: np.random.Generator) -> np.ndarray:
+def pseudo_physical_tensor(cut_role, n_out: int, rng: np.random.Generator, mass: float = 1.0) -> np.ndarray:
     """Random Pauli-basis tensor for a node with the given cut roles (in
-    axis order) and ``n_out`` output bits.  Returns float64 flat data."""
+    axis order) and ``n_out`` output bits.  Every physical variant's
+    distribution over its measured bits has total ``mass`` (1 for a whole
+    node; less when the node's tensor is restricted to one assignment of
+    some output bits).  Returns float64 flat data."""
     ups = [i for i, r in enumerate(cut_role) if r == 0]
     downs = [i for i, r in enumerate(cut_role) if r == 1]
     u, d = len(ups), len(downs)
@@ -122,6 +125,7 @@ def pseudo_physical_tensor(cut_role, n_out: int, rng: np.random.Generator) -> np
     shape = (3,) * u + (4,) * d + (2,) * u + (1 << n_out,)
     p = rng.exponential(1.0, size=shape)
     p /= p.reshape((3 ** u) * (4 ** d), -1).sum(axis=1).reshape((3,) * u + (4,) * d + (1,) * (u + 1))
+    p *= mass
     # upstream cuts contract (basis_t, y_t) -> e_t; downstream cuts contract init_t -> e_t
     labels = list(range(u)) + list(range(u, u + d)) + list(range(u + d, 2 * u + d)) + [2 * u + d]
     ops = [p, labels]
@@ -212,6 +216,39 @@ def pseudo_physical_network(n_qubits: int, edges, outs, seed: int) -> Network:
         data = pseudo_physical_tensor(role, len(outs[j]), rng)
         nodes.append(Node(list(outs[j]), [c for c, _ in cl], role, data))
     net = Network(n_qubits, len(edges), nodes, {"kind": "pseudo_physical", "seed": seed})
+    net.check()
+    return net
+
+
+def bin_restricted_network(n_qubits: int, edges, outs, free_qubits, seed: int, meta=None) -> Network:
+    """The network of one bin, drawn already restricted: node j keeps only
+    its free output bits (the bin fixes the others), so its tensor has
+    4^{c_j} * 2^{F_j} entries instead of 4^{c_j} * 2^{o_j} (§III-E-2 bins;
+    full tensors at these widths would not fit in host memory).  Each
+    physical variant is a random exponential distribution over its measured
+    cut bits and free outputs with total mass 2^{-(fixed outputs of the
+    node)}, the mean share of one fixed assignment.  Free qubits are
+    renumbered 0..F-1 in ascending order; ``meta["free_qubits"]`` keeps the
+    original ids."""
+    free = sorted(int(q) for q in free_qubits)
+    rank = {q: i for i, q in enumerate(free)}
+    rng = np.random.Generator(np.random.PCG64(seed))
+    m = len(outs)
+    cuts = [[] for _ in range(m)]
+    for cid, (a, b) in enumerate(edges):
+        cuts[a].append((cid, 0))
+        cuts[b].append((cid, 1))
+    nodes = []
+    for j in range(m):
+        cl = sorted(cuts[j])
+        role = [r for _, r in cl]
+        f = [rank[q] for q in outs[j] if q in rank]
+        n_fixed = len(outs[j]) - len(f)
+        data = pseudo_physical_tensor(role, len(f), rng, mass=2.0 ** -n_fixed)
+        nodes.append(Node(sorted(f), [c for c, _ in cl], role, data))
+    net = Network(len(free), len(edges), nodes,
+                  {"kind": "bin_restricted_pseudo_physical", "seed": seed, "free_qubits": free,
+                   "n_qubits_full": n_qubits, **(meta or {})})
     net.check()
     return net
 

@@ -9,6 +9,13 @@
 * ``grid30``: the shape of a 30-qubit (5x6) grid cut into 4 subcircuits of
   width 10 with 10 cuts -- a shape-matched network with pseudo-physical
   tensors (a real 5x6 depth-10 grid needs far more than 10 cuts at width 10).
+* ``qaoa48``: 48-qubit QAOA p=1 on a seeded random 3-regular graph, cut by
+  an annealed gate partition into 5 subcircuits of width <= 16 (16-24 wire
+  cuts); one bin of 2^24 states (qubits 0-23 free, the rest fixed), node
+  tensors drawn already restricted to the bin.
+* ``grid64``: the shape of a 64-qubit (8x8) grid cut into 6 subcircuits of
+  width <= 20 with 27 cuts; a stream of bins of 2^24 states (qubits 0-23
+  free), each bin's node tensors drawn already restricted with its own seed.
 * ``small_random``: tiny exact cut circuits for parity and oracle pins.
 """
 from __future__ import annotations
@@ -48,6 +55,56 @@ def grid30(instance: int = 0) -> Network:
     net = tensors.shape_matched_network(30, 4, 10, 10, seed=1000 * 2 + instance, max_node_cuts=7)
     net.meta.update({"workload": "grid30", "circuit": "shape of 5x6 grid, 4 subcircuits, width 10, 10 cuts"})
     return net
+
+
+def qaoa48_shape(instance: int = 0):
+    """(n, edges, outs) of the cut 48-qubit QAOA circuit ``instance``."""
+    seed = 1000 * 4 + instance
+    n, gates = circuits.qaoa_regular(48, seed)
+    for m in (5, 6):
+        try:
+            part = cutter.anneal_partition(n, gates, m, 16, seed=seed + 17 * m, free_qubits=range(24),
+                                           max_log2_elems=24)
+        except RuntimeError:
+            continue
+        cc = cutter.cut_circuit(n, gates, part)
+        if 16 <= cc.n_cuts <= 24:
+            edges, outs = cutter.network_shape(cc)
+            return n, edges, outs
+    raise RuntimeError(f"qaoa48 instance {instance}: no partition with 16..24 cuts")
+
+
+def qaoa48(instance: int = 0, free_qubits=tuple(range(24))) -> Network:
+    n, edges, outs = qaoa48_shape(instance)
+    net = tensors.bin_restricted_network(n, edges, outs, free_qubits, seed=1000 * 4 + 500 + instance,
+                                         meta={"workload": "qaoa48", "edges": edges,
+                                               "circuit": "QAOA p=1, 3-regular graph, n=48"})
+    return net
+
+
+def grid64_shape(instance: int = 0):
+    """(n, edges, outs) of the 64-qubit grid shape: 6 nodes, 27 cuts, width <= 20."""
+    rng = np.random.Generator(np.random.PCG64(1000 * 5 + instance))
+    for _ in range(1000):
+        edges, outs = tensors.sample_shape(64, 6, 27, 20, rng, max_node_cuts=10)
+        # keep every bin-restricted node tensor within 2^24 entries
+        c = np.zeros(6, dtype=int)
+        for a, b in edges:
+            c[a] += 1
+            c[b] += 1
+        f = np.array([sum(q < 24 for q in o) for o in outs])
+        if np.all(2 * c + f <= 24):
+            return 64, edges, outs
+    raise RuntimeError("grid64: no shape within the node size cap")
+
+
+def grid64_bin(instance: int = 0, bin_index: int = 0, free_qubits=tuple(range(24))) -> Network:
+    """Bin ``bin_index`` of the stream: same shape, own seeded tensors."""
+    n, edges, outs = grid64_shape(instance)
+    return tensors.bin_restricted_network(n, edges, outs, free_qubits,
+                                          seed=1000 * 5 + 100 * (instance + 1) + bin_index,
+                                          meta={"workload": "grid64", "bin": bin_index, "edges": edges,
+                                                "circuit": "shape of 8x8 grid, 6 subcircuits, width <= 20, 27 cuts"})
 
 
 def random_cut_circuit(seed: int, n: int, depth: int, n_sub: int, family: str = "line"):

@@ -7,11 +7,14 @@ It shares no code with the CUDA library and never imports it.
 * **Oracle A** (:func:`recon_states`): the reconstruction formula (Eq.
   reconstruction, §II-A) with the factor 1/2 per cut, brute force over all
   4^|E| cut assignments per state, in plain C (``recon_bruteforce.c``).
-* **Oracle B** (:func:`recon_states_elim`): per-state variable elimination
-  in numpy FP64 -- fix x, each node becomes a tensor over its cuts, and the
-  cuts are summed out one by one in ascending id.  A different algorithm from
-  oracle A and from any contraction plan; used where 4^|E| per state is too
-  slow, and checked against oracle A on small networks.
+* **Oracle B** (:func:`recon_states_elim`): per-state elimination in numpy
+  FP64 -- fix x, each node becomes a tensor over its cuts, and factors are
+  contracted two at a time over all the cuts they share (``tensordot``),
+  always the pair with the smallest result first, until one scalar is left.
+  Only the order of the sums in the formula changes (distributivity).  A
+  different algorithm from oracle A, with no bit layouts, bins or tiles;
+  used where 4^|E| per state is too slow, and checked against oracle A on
+  small networks.
 * :func:`total_mass`: Z = sum_x P(x) over the full output space.  Because the
   nodes' outputs partition the qubits, the sum over x splits into one sum per
   node, so Z = 2^{-|E|} sum_e prod_j S_j[e], S_j[e] = sum_x T_j[e][x].
@@ -133,39 +136,46 @@ def _node_cut_tensor(nd, state: int) -> np.ndarray:
     return nd.tensor()[..., x]
 
 
-def _eliminate(factors, n_cuts: int) -> float:
-    """Sum out cut variables 0..n_cuts-1 in order from a list of (axes, tensor)."""
-    for c in range(n_cuts):
-        bucket = [f for f in factors if c in f[0]]
-        rest = [f for f in factors if c not in f[0]]
-        union = sorted(set().union(*[set(ax) for ax, _ in bucket]))
-        keep = [a for a in union if a != c]
-        label = {a: i for i, a in enumerate(union)}
-        ops = []
-        for ax, t in bucket:
-            ops += [t, [label[a] for a in ax]]
-        ops.append([label[a] for a in keep])
-        factors = rest + [(keep, np.einsum(*ops))]
-    val = 1.0
-    for ax, t in factors:
-        assert not ax
-        val *= float(t)
-    return val
+def _contract_pairs(factors) -> float:
+    """Sum out every cut of a list of (axes, tensor) factors, in which each
+    cut appears in exactly two factors: repeatedly contract the two factors
+    whose result (the cuts in one but not both) is smallest -- ties to the
+    lowest pair of positions -- over all the cuts they share."""
+    factors = [(list(ax), np.asarray(t, dtype=np.float64)) for ax, t in factors]
+    while len(factors) > 1:
+        best = None
+        for i in range(len(factors)):
+            for j in range(i + 1, len(factors)):
+                ai, aj = set(factors[i][0]), set(factors[j][0])
+                if not ai & aj and best is not None:
+                    continue
+                size = len(ai ^ aj)
+                if best is None or size < best[0] or (best[3] == 0 and ai & aj):
+                    best = (size, i, j, len(ai & aj))
+        _, i, j, _ = best
+        (ax_i, t_i), (ax_j, t_j) = factors[i], factors[j]
+        shared = [a for a in ax_i if a in ax_j]
+        t = np.tensordot(t_i, t_j, axes=([ax_i.index(a) for a in shared], [ax_j.index(a) for a in shared]))
+        ax = [a for a in ax_i if a not in shared] + [a for a in ax_j if a not in shared]
+        factors = [f for k, f in enumerate(factors) if k not in (i, j)] + [(ax, t)]
+    ax, t = factors[0]
+    assert not ax, "every cut must appear in exactly two factors"
+    return float(t)
 
 
 def recon_states_elim(net, states) -> np.ndarray:
-    """Oracle B: per-state variable elimination in FP64."""
+    """Oracle B: P(x) per state by pairwise elimination of the cut sums in FP64."""
     out = np.empty(len(states), dtype=np.float64)
     for s_i, s in enumerate(states):
         factors = [(list(nd.cut_ids), _node_cut_tensor(nd, int(s))) for nd in net.nodes]
-        out[s_i] = np.ldexp(_eliminate(factors, net.n_cuts), -net.n_cuts)
+        out[s_i] = np.ldexp(_contract_pairs(factors), -net.n_cuts)
     return out
 
 
 def total_mass(net) -> float:
     """Z = sum over all 2^n states of P(x), via per-node output sums."""
     factors = [(list(nd.cut_ids), nd.tensor().sum(axis=-1)) for nd in net.nodes]
-    return float(np.ldexp(_eliminate(factors, net.n_cuts), -net.n_cuts))
+    return float(np.ldexp(_contract_pairs(factors), -net.n_cuts))
 
 
 def timed_sample(net, states, n_threads: int = 0):

@@ -155,3 +155,81 @@ def test_shape_matched_widths():
         o = np.array([len(x) for x in outs])
         w = o + u                 # width = outputs + measured cuts = initial + initialised
         assert np.all(w <= 10) and o.sum() == 30 and len(edges) == 10
+
+
+def test_anneal_partition_matches_cut_circuit():
+    n, gates = circuits.qaoa_regular(12, 77)
+    part = cutter.anneal_partition(n, gates, 3, 8, seed=3, iters=3000)
+    cc = cutter.cut_circuit(n, gates, part)
+    assert len(cc.subs) == 3 and max(cutter.widths(cc)) <= 8
+    # the annealer's own cut / width count agrees with the cutter
+    multi = [g for g, (_, qs, _) in enumerate(gates) if len(qs) > 1]
+    wire_gates = [[g for g in multi if q in gates[g][1]] for q in range(n)]
+    cuts, w, c, f = cutter._partition_cost(n, wire_gates, {g: part[g] for g in multi}, 3, set(range(n)))
+    assert cuts == cc.n_cuts and list(w) == cutter.widths(cc)
+    edges, outs = cutter.network_shape(cc)
+    assert sorted(q for o in outs for q in o) == list(range(n))
+    assert list(c) == [sum(a == j for a, _ in edges) + sum(b == j for _, b in edges) for j in range(3)]
+    assert list(f) == [len(o) for o in outs]
+
+
+def _node_cuts(edges, m):
+    c = np.zeros(m, dtype=int)
+    for a, b in edges:
+        c[a] += 1
+        c[b] += 1
+    return c
+
+
+def test_qaoa48_shape_within_stated_sizes():
+    n, edges, outs = workloads.qaoa48_shape(0)
+    m = len(outs)
+    assert n == 48 and 16 <= len(edges) <= 24 and m >= 5
+    u = np.array([sum(a == j for a, _ in edges) for j in range(m)])
+    o = np.array([len(x) for x in outs])
+    assert np.all(o + u <= 16)                 # width = outputs + measured cuts
+    assert sorted(q for x in outs for q in x) == list(range(48))
+    f = np.array([sum(q < 24 for q in x) for x in outs])
+    assert np.all(2 * _node_cuts(edges, m) + f <= 24)
+
+
+def test_grid64_shape_within_stated_sizes():
+    n, edges, outs = workloads.grid64_shape(0)
+    m = len(outs)
+    assert n == 64 and 24 <= len(edges) <= 30
+    u = np.array([sum(a == j for a, _ in edges) for j in range(m)])
+    o = np.array([len(x) for x in outs])
+    assert np.all(o + u <= 20) and o.sum() == 64
+    f = np.array([sum(q < 24 for q in x) for x in outs])
+    assert np.all(2 * _node_cuts(edges, m) + f <= 24)
+
+
+def test_bin_restricted_with_every_qubit_free_is_the_full_network():
+    rng = np.random.Generator(np.random.PCG64(11))
+    edges, outs = tensors.sample_shape(12, 3, 4, 8, rng)
+    full = tensors.pseudo_physical_network(12, edges, outs, seed=5)
+    restricted = tensors.bin_restricted_network(12, edges, outs, range(12), seed=5)
+    for a, b in zip(full.nodes, restricted.nodes):
+        assert a.out_qubits == b.out_qubits and a.cut_ids == b.cut_ids
+        np.testing.assert_array_equal(a.data, b.data)
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_bin_restricted_trace_identities_scale_with_fixed_outputs(seed):
+    """A node with k fixed outputs keeps the trace identities scaled by
+    2^-k: each variant's distribution over the free outputs has mass 2^-k."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    edges, outs = tensors.sample_shape(14, 3, 5, 9, rng)
+    free = sorted(rng.choice(14, size=8, replace=False).tolist())
+    net = tensors.bin_restricted_network(14, edges, outs, free, seed=seed)
+    assert net.n_qubits == 8 and net.meta["free_qubits"] == free
+    for j, nd in enumerate(net.nodes):
+        k = len(outs[j]) - nd.n_out
+        S = nd.tensor().sum(axis=-1)
+        ups, downs = _up_down(nd)
+        for ed in itertools.product(range(4), repeat=len(downs)):
+            idx = [0] * nd.n_cut
+            for ax, v in zip(downs, ed):
+                idx[ax] = v
+            want = 2.0 ** (len(downs) - k) if all(v == 0 for v in ed) else 0.0
+            assert abs(S[tuple(idx)] - want) < 1e-11
