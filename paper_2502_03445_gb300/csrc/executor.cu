@@ -147,6 +147,8 @@ std::vector<int> tile_candidates(const StepPlan &st) {
     if (st.klass == KC_UMMA) {
         if (st.nb >= 7) c.push_back(UMMA_128x128);
         c.push_back(UMMA_128x64);
+        if (st.mb >= 7 && st.nb >= 7) c.push_back(UMMA_128x128_DEEP);
+        if (st.mb >= 7 && st.nb >= 8) c.push_back(UMMA_128x256_DEEP);
     } else {
         c.push_back(SIMT_64x64);
         if (st.mb >= 7 && st.nb >= 6) c.push_back(SIMT_128x64);
@@ -156,6 +158,21 @@ std::vector<int> tile_candidates(const StepPlan &st) {
 }
 
 }  // namespace
+
+// Without autotuning: big tiles for big steps.  A long K loop (K >= 2^12)
+// over whole 128-row tiles takes the deep-K tensor-core form: 128 x 256
+// tiles when N allows (1.3-1.5x over 128 x 128 at K = 2^14 in every
+// precision), 128 x 128 ones only for split BF16 (slower than the staged
+// 128 x 128 form in plain BF16 and TF32).
+int default_step_tile(const StepPlan &st) {
+    if (st.klass == KC_UMMA) {
+        const bool deep = st.kb >= DEEP_MIN_LOG2_K && st.mb >= 7;
+        if (deep && st.nb >= 8) return UMMA_128x256_DEEP;
+        if (deep && st.nb == 7 && st.prec == TQC_PREC_BF16X3) return UMMA_128x128_DEEP;
+        return st.nb >= 7 ? UMMA_128x128 : UMMA_128x64;
+    }
+    return (st.mb >= 7 && st.nb >= 7) ? SIMT_128x128 : (st.mb >= 7 && st.nb >= 6 ? SIMT_128x64 : SIMT_64x64);
+}
 
 IngestArgs exec_leaf_args(const Plan &p, const TensorPlan &t, int j, const uint8_t *fixed) {
     return leaf_args(p, t, j, fixed, 0, false);
@@ -256,8 +273,7 @@ tqc_status exec_prepare(Plan *p) {
     TQC_CUDA(cudaMemset(p->d_zinfo, 0, 4 * sizeof(double) + 64), "memset");
     // tile choice without autotuning: big tiles for big steps
     for (auto &st : p->steps) {
-        if (st.klass == KC_UMMA) st.tile = st.nb >= 7 ? UMMA_128x128 : UMMA_128x64;
-        else st.tile = (st.mb >= 7 && st.nb >= 7) ? SIMT_128x128 : (st.mb >= 7 && st.nb >= 6 ? SIMT_128x64 : SIMT_64x64);
+        st.tile = default_step_tile(st);
     }
     p->ready = true;
     return TQC_OK;

@@ -26,7 +26,8 @@ cudaError_t launch_finalize(const double *acc, void *out, int out_f64, const dou
                             cudaStream_t s);
 
 // tcgen05 step (umma.cu)
-enum UmmaCfg { UMMA_128x128 = 0, UMMA_128x64 = 1, UMMA_N_CFG = 2 };
+// *_DEEP: direct epilogue and a deeper operand ring, for steps with a long K loop
+enum UmmaCfg { UMMA_128x128 = 0, UMMA_128x64 = 1, UMMA_128x128_DEEP = 2, UMMA_128x256_DEEP = 3, UMMA_N_CFG = 4 };
 TileShape umma_tile(int cfg);
 // prec: TQC_PREC_BF16 / TQC_PREC_BF16X3 / TQC_PREC_TF32
 cudaError_t launch_umma_step(int cfg, int prec, const StepArgs &a, int *d_err, cudaStream_t s);
@@ -36,6 +37,10 @@ cudaError_t umma_make_maps(int prec, const StepArgs &a, int bn, void *maps_out);
 IngestArgs exec_leaf_args(const Plan &p, const TensorPlan &t, int j, const uint8_t *fixed);
 StepArgs exec_step_args(const Plan &p, const StepPlan &st, TileShape tile);
 int exec_epi_mode(int storage);
+
+// Tile configuration of a step when it is not autotuned.
+constexpr int DEEP_MIN_LOG2_K = 12;
+int default_step_tile(const StepPlan &st);
 
 // Epilogue parameters for a step given its result masks and tile shape.
 EpiParams make_epi(uint64_t maskR, uint64_t maskC, int mb, int nb, TileShape t);

@@ -128,8 +128,7 @@ extern "C" tqc_status tqc_contract_noalloc(tqc_plan_t plan, const void *const *d
     p.profile = 0;
     net.device = dev;
     for (auto &st : p.steps) {  // the tile rule of the allocating path
-        if (st.klass == KC_UMMA) st.tile = st.nb >= 7 ? UMMA_128x128 : UMMA_128x64;
-        else st.tile = (st.mb >= 7 && st.nb >= 7) ? SIMT_128x128 : (st.mb >= 7 && st.nb >= 6 ? SIMT_128x64 : SIMT_64x64);
+        st.tile = default_step_tile(st);
     }
     tqc_status st = exec_contract(&p, fixed_bits, d_out, out_dtype, nullptr, cuda_stream);
     // restore

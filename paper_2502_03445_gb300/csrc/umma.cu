@@ -14,9 +14,15 @@
 //   warp 1      allocates TMEM (two FP32 accumulators of 128 x BN) and issues
 //               tcgen05.mma from one thread; tcgen05.commit frees stages and
 //               hands accumulators to the epilogue
-//   warps 2..5  epilogue: tcgen05.ld 32 columns at a time, stage the tile in
+//   warps 2..17 epilogue: tcgen05.ld 32 columns at a time, stage the tile in
 //               shared memory in the orientation that makes the result's
 //               lowest bits contiguous, then write 16-byte runs to HBM
+// The deep-K form (K of thousands, few output tiles) drops the staging
+// buffers: every epilogue warp loads its 32 x 32 block from TMEM, frees the
+// accumulator and stores straight to HBM, which the next tile's long K loop
+// hides; the freed shared memory deepens the operand ring (192 KB in
+// flight) and allows 128 x 256 MMA tiles, since that loop is bound by the
+// latency of the copies, not by the tensor pipe.
 // Every wait is bounded (clock64); a wait that gives up sets an error word,
 // drains the copies and MMAs it issued, frees TMEM and returns.
 #include <cuda.h>
@@ -51,7 +57,7 @@ struct UmmaParams {
     int *err;
 };
 
-template <int BN, int KIND>
+template <int BN, int KIND, bool DEEP>
 struct Cfg {
     static constexpr int ELEM = KIND == K_TF32 ? 4 : 2;
     static constexpr int BK = 128 / ELEM;          // one 128-byte swizzle atom of K
@@ -59,15 +65,17 @@ struct Cfg {
     static constexpr int A_BYTES = BM * 128;
     static constexpr int B_BYTES = BN * 128;
     static constexpr int STAGE_BYTES = PLANES * (A_BYTES + B_BYTES);
-    static constexpr int STAGES = KIND == K_BF16X3 ? 2 : (BN == 64 ? 6 : 4);
+    static constexpr int STAGES = DEEP ? 196608 / STAGE_BYTES : (KIND == K_BF16X3 ? 2 : (BN == 64 ? 6 : 4));
     static constexpr int SUB_N = 64;               // epilogue sub-tile: 128 x 64
     static constexpr int PITCH_R = SUB_N + 4;      // row-major staging pitch (floats)
     static constexpr int PITCH_C = BM + 4;         // column-major staging pitch
     static constexpr int STG_FLOATS = BM * PITCH_R > SUB_N * PITCH_C ? BM * PITCH_R : SUB_N * PITCH_C;
-    static constexpr int STG_BYTES = 2 * STG_FLOATS * 4;  // two buffers (ping-pong)
+    static constexpr int STG_BYTES = DEEP ? 0 : 2 * STG_FLOATS * 4;  // two buffers (ping-pong)
     static constexpr int BAR_BYTES = 512;
     static constexpr int SMEM = 1024 + STAGES * STAGE_BYTES + STG_BYTES + (int)sizeof(EpiTables) + BAR_BYTES;
     static constexpr int TMEM_COLS = 2 * BN;
+    static_assert(SMEM <= 232448, "shared memory per CTA");
+    static_assert(STAGES >= 2, "operand ring");
     // instruction descriptor: D = F32, A/B = BF16 (1) or TF32 (2), K-major, N >> 3, M >> 4
     static constexpr uint32_t IDESC = (1u << 4) | ((KIND == K_TF32 ? 2u : 1u) << 7) |
                                       ((KIND == K_TF32 ? 2u : 1u) << 10) | ((uint32_t)(BN >> 3) << 17) |
@@ -173,12 +181,12 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
 }
 
 
-template <int BN, int KIND>
+template <int BN, int KIND, bool DEEP>
 __global__ void __launch_bounds__(NTHREADS, 1)
     umma_step_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tB,
                      const __grid_constant__ CUtensorMap tAl, const __grid_constant__ CUtensorMap tBl,
                      const UmmaParams P) {
-    using C = Cfg<BN, KIND>;
+    using C = Cfg<BN, KIND, DEEP>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t *stages = smem;
@@ -202,7 +210,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         }
         for (int a = 0; a < 2; ++a) {
             mbar_init(&tfull[a], 1);
-            mbar_init(&tempty[a], STAGE_WARPS);
+            mbar_init(&tempty[a], DEEP ? EPI_WARPS : STAGE_WARPS);
         }
         mbar_init(drain, 1);
         *abort_flag = 0;
@@ -299,6 +307,64 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             umma_commit(drain);
             long long t0 = clock64();
             while (!mbar_try_wait(drain, 0) && clock64() - t0 < WAIT_CYCLES) {
+            }
+        }
+    } else if constexpr (DEEP) {
+        // ------------------------------------------------ direct epilogue
+        // Warp (lane group g, quarter q) owns accumulator rows 32g..32g+31
+        // and the 32-column chunks q, q + 4, ...; it frees the accumulator as
+        // soon as its loads land and then stores every value to its place in
+        // the result layout: offset = tile base + G_row[r] + G_col[c], both
+        // parts deposits of the tile-local row / column bits.
+        constexpr int CH = BN / 128;     // chunks per warp
+        constexpr int SUBS = BN / C::SUB_N;
+        const int q = (warp - 2) >> 2;
+        const int lane_grp = warp & 3;
+        const int row = lane_grp * 32 + lane;
+        const int etid = threadIdx.x - 64;
+        uint64_t *gcol = (uint64_t *)tb;  // G_col of the 64 columns of a sub-tile
+        if (etid < C::SUB_N) gcol[etid] = pdep64((uint64_t)pdep32((uint32_t)etid, e.lowCc), e.tileMask);
+        asm volatile("bar.sync 1, %0;" ::"n"(EPI_THREADS) : "memory");
+        const uint64_t grow = pdep64((uint64_t)pdep32((uint32_t)row, e.lowRc), e.tileMask);
+        const double sc = (e.mode == EPI_OUT_F32 || e.mode == EPI_OUT_F64) ? e.zinfo[1] : 1.0;
+        // four consecutive columns are four consecutive elements when the two
+        // lowest tile bits are column bits at result bits 0 and 1
+        const bool vec4 = (e.lowCc & 3u) == 3u && e.L >= 2;
+        int64_t lt = 0;
+        for (int64_t tile = blockIdx.x; tile < P.n_tiles; tile += gridDim.x, ++lt) {
+            const int acc = (int)(lt & 1);
+            if (lane == 0) mbar_wait(&tfull[acc], (uint32_t)((lt >> 1) & 1), abort_flag);
+            __syncwarp();
+            if (*abort_flag) break;
+            tc_fence_after();
+            uint32_t r[CH][32];
+#pragma unroll
+            for (int c = 0; c < CH; ++c)
+                tmem_ld32(tmem_base + ((uint32_t)(lane_grp * 32) << 16) + (uint32_t)(acc * BN + (q + 4 * c) * 32), r[c]);
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tempty[acc]);
+            const uint64_t rt = (uint64_t)(tile / P.col_tiles);
+            const uint64_t ct = (uint64_t)(tile - (int64_t)rt * P.col_tiles);
+#pragma unroll
+            for (int c = 0; c < CH; ++c) {
+                const int col0 = (q + 4 * c) * 32;
+                const uint64_t o = tile_base(e, rt, ct * SUBS + (uint64_t)(col0 / C::SUB_N)) + grow;
+                const uint64_t *gc = gcol + (col0 % C::SUB_N);
+                if (vec4) {
+#pragma unroll
+                    for (int j = 0; j < 32; j += 4) {
+                        const float v[4] = {__uint_as_float(r[c][j]), __uint_as_float(r[c][j + 1]),
+                                            __uint_as_float(r[c][j + 2]), __uint_as_float(r[c][j + 3])};
+                        store_run_f32(e, o + gc[j], v, 4, sc);
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        const float v = __uint_as_float(r[c][j]);
+                        store_run_f32(e, o + gc[j], &v, 1, sc);
+                    }
+                }
             }
         }
     } else {
@@ -493,14 +559,18 @@ cudaError_t encode(CUtensorMap *m, const void *ptr, int elem, uint64_t k, uint64
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-template <int BN, int KIND>
+template <int BN, int KIND, bool DEEP>
 cudaError_t launch_kind(const StepArgs &a, int *d_err, cudaStream_t s) {
-    using C = Cfg<BN, KIND>;
+    using C = Cfg<BN, KIND, DEEP>;
+    constexpr int lbn = BN == 256 ? 8 : (BN == 128 ? 7 : 6);
+    // the direct epilogue writes whole 128 x BN tiles
+    if (DEEP && (a.epi.a_bits != 7 || a.epi.b_bits != 6 || a.nb < lbn)) return cudaErrorInvalidValue;
     cudaError_t e = get_encode();
     if (e != cudaSuccess) return e;
     static bool attr = false;
     if (!attr) {
-        e = cudaFuncSetAttribute(umma_step_kernel<BN, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+        e = cudaFuncSetAttribute(umma_step_kernel<BN, KIND, DEEP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 C::SMEM);
         if (e != cudaSuccess) return e;
         attr = true;
     }
@@ -519,8 +589,7 @@ cudaError_t launch_kind(const StepArgs &a, int *d_err, cudaStream_t s) {
     UmmaParams p;
     p.epi = a.epi;
     // MMA tiles are 128 x BN; the epilogue parameters describe 128 x 64 sub-tiles
-    const int lbn = BN == 128 ? 7 : 6;
-    if (BN == 128 && a.nb < 7) return cudaErrorInvalidValue;
+    if (BN >= 128 && a.nb < lbn) return cudaErrorInvalidValue;
     const int64_t row_tiles = (int64_t)1 << (a.mb - a.epi.a_bits);
     p.col_tiles = a.nb >= lbn ? (int64_t)1 << (a.nb - lbn) : 1;
     p.n_tiles = row_tiles * p.col_tiles;
@@ -530,16 +599,16 @@ cudaError_t launch_kind(const StepArgs &a, int *d_err, cudaStream_t s) {
     p.gmode = pk.gmode;
     p.err = d_err;
     const int64_t grid = std::min<int64_t>(p.n_tiles, sm_count());
-    umma_step_kernel<BN, KIND><<<(unsigned)grid, NTHREADS, C::SMEM, s>>>(tA, tB, tAl, tBl, p);
+    umma_step_kernel<BN, KIND, DEEP><<<(unsigned)grid, NTHREADS, C::SMEM, s>>>(tA, tB, tAl, tBl, p);
     return cudaGetLastError();
 }
 
-template <int BN>
+template <int BN, bool DEEP>
 cudaError_t launch_bn(int prec, const StepArgs &a, int *d_err, cudaStream_t s) {
     switch (prec) {
-        case TQC_PREC_BF16: return launch_kind<BN, K_BF16>(a, d_err, s);
-        case TQC_PREC_BF16X3: return launch_kind<BN, K_BF16X3>(a, d_err, s);
-        case TQC_PREC_TF32: return launch_kind<BN, K_TF32>(a, d_err, s);
+        case TQC_PREC_BF16: return launch_kind<BN, K_BF16, DEEP>(a, d_err, s);
+        case TQC_PREC_BF16X3: return launch_kind<BN, K_BF16X3, DEEP>(a, d_err, s);
+        case TQC_PREC_TF32: return launch_kind<BN, K_TF32, DEEP>(a, d_err, s);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -568,15 +637,20 @@ cudaError_t umma_make_maps(int prec, const StepArgs &a, int bn, void *maps_out) 
     return cudaSuccess;
 }
 
-// Epilogue tile of both configurations (the MMA tile is 128 x 128 or 128 x 64).
+// Epilogue tile of every configuration (the MMA tile is 128 x 64, 128 x 128 or 128 x 256).
 TileShape umma_tile(int cfg) {
     (void)cfg;
     return TileShape{7, 6};
 }
 
 cudaError_t launch_umma_step(int cfg, int prec, const StepArgs &a, int *d_err, cudaStream_t s) {
-    if (cfg == UMMA_128x64) return launch_bn<64>(prec, a, d_err, s);
-    return launch_bn<128>(prec, a, d_err, s);
+    switch (cfg) {
+        case UMMA_128x64: return launch_bn<64, false>(prec, a, d_err, s);
+        case UMMA_128x128: return launch_bn<128, false>(prec, a, d_err, s);
+        case UMMA_128x128_DEEP: return launch_bn<128, true>(prec, a, d_err, s);
+        case UMMA_128x256_DEEP: return launch_bn<256, true>(prec, a, d_err, s);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 }  // namespace tqc

@@ -235,6 +235,45 @@ def test_tensor_core_step_bf16_tf32(prec, fa, fb, cuts, low_a):
     check_tc(prec, got, net, d)
 
 
+# Deep-K steps (K = 4^6, 4^7): the default tile is the direct-epilogue form,
+# 128 x 256 when N >= 256, 128 x 128 for split BF16 when N = 128.
+UMMA_128x128, UMMA_128x64, UMMA_128x128_DEEP, UMMA_128x256_DEEP = 0, 1, 2, 3
+DEEP_CASES = [  # (fa, fb, cuts, qubit 0 on rows)
+    (8, 8, 6, True), (9, 8, 6, False), (9, 7, 6, True), (7, 8, 7, False),
+]
+
+
+def expected_deep_tile(d, prec):
+    st = d["steps"][-1]
+    if st["log2_n"] >= 8:
+        return UMMA_128x256_DEEP
+    return UMMA_128x128_DEEP if prec == "bf16x3" else UMMA_128x128
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "bf16", "tf32"])
+@pytest.mark.parametrize("fa,fb,cuts,low_a", DEEP_CASES)
+def test_tensor_core_deep_k(prec, fa, fb, cuts, low_a):
+    net = two_node(1300 + fa * 7 + cuts, fa, fb, cuts, low_a)
+    got, z, d = run(net, precision=prec)
+    st = d["steps"][-1]
+    assert st["class"] == "tcgen05" and st["log2_k"] == 2 * cuts
+    assert st["tile"] == expected_deep_tile(d, prec), st
+    want = oracle.recon_bin(net)
+    if prec == "bf16x3":
+        check_fp32(got, want)
+    else:
+        check_tc(prec, got, net, d, want)
+
+
+def test_tensor_core_deep_k_sliced_f64():
+    """Deep-K final step accumulating slices into the FP64 sum."""
+    net = two_node(1400, 8, 8, 7, True)
+    want = oracle.recon_bin(net)
+    got, z, d = run(net, precision="bf16x3", sliced=[2], out_f64=True)
+    assert d["sliced"] == [2] and d["steps"][-1]["tile"] == UMMA_128x256_DEEP
+    check_fp32(got, want)
+
+
 def abs_mass(net):
     """sum_x of the reconstruction with |T_j| in place of T_j: the sum of
     the absolute values of every term, which bounds rounding errors."""
