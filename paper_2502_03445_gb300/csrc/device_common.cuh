@@ -73,7 +73,7 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
     return *(uint32_t *)&p;
 }
 
-// Store `vw` (1 or 4) values to consecutive elements starting at `off`;
+// Store `vw` (1, 2 or 4) values to consecutive elements starting at `off`;
 // `s` is the output scale zinfo[1] for the EPI_OUT_* modes (read once per
 // tile by the caller).
 __device__ __forceinline__ void store_run_f32(const EpiParams &e, uint64_t off, const float *v, int vw,
@@ -82,16 +82,19 @@ __device__ __forceinline__ void store_run_f32(const EpiParams &e, uint64_t off, 
         case EPI_F32: {
             float *o = (float *)e.out + off;
             if (vw == 4) *(float4 *)o = make_float4(v[0], v[1], v[2], v[3]);
+            else if (vw == 2) *(float2 *)o = make_float2(v[0], v[1]);
             else o[0] = v[0];
         } break;
         case EPI_TF32: {
             float *o = (float *)e.out + off;
             if (vw == 4) *(float4 *)o = make_float4(to_tf32(v[0]), to_tf32(v[1]), to_tf32(v[2]), to_tf32(v[3]));
+            else if (vw == 2) *(float2 *)o = make_float2(to_tf32(v[0]), to_tf32(v[1]));
             else o[0] = to_tf32(v[0]);
         } break;
         case EPI_BF16: {
             __nv_bfloat16 *o = (__nv_bfloat16 *)e.out + off;
             if (vw == 4) *(uint2 *)o = make_uint2(pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]));
+            else if (vw == 2) *(uint32_t *)o = pack_bf16x2(v[0], v[1]);
             else o[0] = __float2bfloat16_rn(v[0]);
         } break;
         case EPI_BF16X2: {
@@ -106,6 +109,9 @@ __device__ __forceinline__ void store_run_f32(const EpiParams &e, uint64_t off, 
             if (vw == 4) {
                 *(uint2 *)oh = make_uint2(pack_bf16x2(h[0], h[1]), pack_bf16x2(h[2], h[3]));
                 *(uint2 *)ol = make_uint2(pack_bf16x2(l[0], l[1]), pack_bf16x2(l[2], l[3]));
+            } else if (vw == 2) {
+                *(uint32_t *)oh = pack_bf16x2(h[0], h[1]);
+                *(uint32_t *)ol = pack_bf16x2(l[0], l[1]);
             } else {
                 oh[0] = __float2bfloat16_rn(h[0]);
                 ol[0] = __float2bfloat16_rn(l[0]);
@@ -116,6 +122,8 @@ __device__ __forceinline__ void store_run_f32(const EpiParams &e, uint64_t off, 
             if (vw == 4) {
                 ((double2 *)o)[0] = make_double2(v[0], v[1]);
                 ((double2 *)o)[1] = make_double2(v[2], v[3]);
+            } else if (vw == 2) {
+                ((double2 *)o)[0] = make_double2(v[0], v[1]);
             } else {
                 o[0] = v[0];
             }
@@ -126,6 +134,9 @@ __device__ __forceinline__ void store_run_f32(const EpiParams &e, uint64_t off, 
                 double2 a = ((double2 *)o)[0], b = ((double2 *)o)[1];
                 ((double2 *)o)[0] = make_double2(a.x + v[0], a.y + v[1]);
                 ((double2 *)o)[1] = make_double2(b.x + v[2], b.y + v[3]);
+            } else if (vw == 2) {
+                double2 a = ((double2 *)o)[0];
+                ((double2 *)o)[0] = make_double2(a.x + v[0], a.y + v[1]);
             } else {
                 o[0] += v[0];
             }
@@ -134,6 +145,7 @@ __device__ __forceinline__ void store_run_f32(const EpiParams &e, uint64_t off, 
             const float sf = (float)s;
             float *o = (float *)e.out + off;
             if (vw == 4) *(float4 *)o = make_float4(v[0] * sf, v[1] * sf, v[2] * sf, v[3] * sf);
+            else if (vw == 2) *(float2 *)o = make_float2(v[0] * sf, v[1] * sf);
             else o[0] = v[0] * sf;
         } break;
         case EPI_OUT_F64: {
@@ -141,6 +153,8 @@ __device__ __forceinline__ void store_run_f32(const EpiParams &e, uint64_t off, 
             if (vw == 4) {
                 ((double2 *)o)[0] = make_double2(v[0] * s, v[1] * s);
                 ((double2 *)o)[1] = make_double2(v[2] * s, v[3] * s);
+            } else if (vw == 2) {
+                ((double2 *)o)[0] = make_double2(v[0] * s, v[1] * s);
             } else {
                 o[0] = v[0] * s;
             }
@@ -251,6 +265,133 @@ __device__ __forceinline__ void epi_readout(const EpiTables *tb, const float *st
             store_run_f32(e, base + tb->g_hi[t >> 7] + tb->g_lo[t & 127], &v, 1, s);
         }
     }
+}
+
+
+// Store VW (1, 2 or 4) consecutive values of an epilogue in output mode MODE
+// (the compile-time twin of store_run_f32, for loops that dispatch the mode
+// once instead of per store); sf / sd: the EPI_OUT_* scale in FP32 / FP64.
+template <int MODE, int VW>
+__device__ __forceinline__ void store_vals(const EpiParams &e, uint64_t off, const float *v, float sf, double sd) {
+    if constexpr (MODE == EPI_F32 || MODE == EPI_TF32 || MODE == EPI_OUT_F32) {
+        float w[VW];
+#pragma unroll
+        for (int i = 0; i < VW; ++i)
+            w[i] = MODE == EPI_TF32 ? to_tf32(v[i]) : (MODE == EPI_OUT_F32 ? v[i] * sf : v[i]);
+        float *o = (float *)e.out + off;
+        if constexpr (VW == 4) *(float4 *)o = make_float4(w[0], w[1], w[2], w[3]);
+        else if constexpr (VW == 2) *(float2 *)o = make_float2(w[0], w[1]);
+        else o[0] = w[0];
+    } else if constexpr (MODE == EPI_BF16) {
+        __nv_bfloat16 *o = (__nv_bfloat16 *)e.out + off;
+        if constexpr (VW == 4) *(uint2 *)o = make_uint2(pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]));
+        else if constexpr (VW == 2) *(uint32_t *)o = pack_bf16x2(v[0], v[1]);
+        else o[0] = __float2bfloat16_rn(v[0]);
+    } else if constexpr (MODE == EPI_BF16X2) {
+        float h[VW], l[VW];
+#pragma unroll
+        for (int i = 0; i < VW; ++i) {
+            h[i] = __bfloat162float(__float2bfloat16_rn(v[i]));
+            l[i] = v[i] - h[i];
+        }
+        __nv_bfloat16 *oh = (__nv_bfloat16 *)e.out + off;
+        __nv_bfloat16 *ol = (__nv_bfloat16 *)e.out_lo + off;
+        if constexpr (VW == 4) {
+            *(uint2 *)oh = make_uint2(pack_bf16x2(h[0], h[1]), pack_bf16x2(h[2], h[3]));
+            *(uint2 *)ol = make_uint2(pack_bf16x2(l[0], l[1]), pack_bf16x2(l[2], l[3]));
+        } else if constexpr (VW == 2) {
+            *(uint32_t *)oh = pack_bf16x2(h[0], h[1]);
+            *(uint32_t *)ol = pack_bf16x2(l[0], l[1]);
+        } else {
+            oh[0] = __float2bfloat16_rn(h[0]);
+            ol[0] = __float2bfloat16_rn(l[0]);
+        }
+    } else {  // FP64 modes
+        double w[VW];
+        double *o = (double *)e.out + off;
+#pragma unroll
+        for (int i = 0; i < VW; ++i) w[i] = MODE == EPI_OUT_F64 ? (double)v[i] * sd : (double)v[i];
+        if constexpr (MODE == EPI_F64_ADD) {
+#pragma unroll
+            for (int i = 0; i < VW; i += 2) {
+                if constexpr (VW == 1) {
+                    o[0] += w[0];
+                } else {
+                    const double2 a = ((const double2 *)o)[i / 2];
+                    ((double2 *)o)[i / 2] = make_double2(a.x + w[i], a.y + w[i + 1]);
+                }
+            }
+        } else {
+            if constexpr (VW == 1) {
+                o[0] = w[0];
+            } else {
+#pragma unroll
+                for (int i = 0; i < VW; i += 2) ((double2 *)o)[i / 2] = make_double2(w[i], w[i + 1]);
+            }
+        }
+    }
+}
+
+// Direct stores of 32 consecutive accumulator columns of one row, VW at a
+// time: run j (j = 0, VW, 2 VW, ...) goes to o + x_j, where x_j is the
+// deposit of j into the result bits of the column index; the next deposit
+// is ((x | ~m) + 1) & m with m = those bits minus the VW-run bits.
+template <int MODE, int VW>
+__device__ __forceinline__ void direct_run32(const EpiParams &e, uint64_t o, uint64_t m, const uint32_t *r, float sf,
+                                             double sd) {
+    uint64_t x = 0;
+#pragma unroll
+    for (int j = 0; j < 32; j += VW) {
+        float v[VW];
+#pragma unroll
+        for (int i = 0; i < VW; ++i) v[i] = __uint_as_float(r[j + i]);
+        store_vals<MODE, VW>(e, o + x, v, sf, sd);
+        x = ((x | ~m) + 1) & m;
+    }
+}
+
+template <int MODE>
+__device__ __forceinline__ void direct_run32_vw(const EpiParams &e, int vw, uint64_t o, uint64_t m, const uint32_t *r,
+                                                float sf, double sd) {
+    if (vw == 4) direct_run32<MODE, 4>(e, o, m, r, sf, sd);
+    else if (vw == 2) direct_run32<MODE, 2>(e, o, m, r, sf, sd);
+    else direct_run32<MODE, 1>(e, o, m, r, sf, sd);
+}
+
+// Mode dispatch, once per 32 values.
+__device__ __forceinline__ void direct_run32_any(const EpiParams &e, int vw, uint64_t o, uint64_t m, const uint32_t *r,
+                                                 float sf, double sd) {
+    switch (e.mode) {
+        case EPI_F32: direct_run32_vw<EPI_F32>(e, vw, o, m, r, sf, sd); break;
+        case EPI_TF32: direct_run32_vw<EPI_TF32>(e, vw, o, m, r, sf, sd); break;
+        case EPI_BF16: direct_run32_vw<EPI_BF16>(e, vw, o, m, r, sf, sd); break;
+        case EPI_BF16X2: direct_run32_vw<EPI_BF16X2>(e, vw, o, m, r, sf, sd); break;
+        case EPI_F64_SET: direct_run32_vw<EPI_F64_SET>(e, vw, o, m, r, sf, sd); break;
+        case EPI_F64_ADD: direct_run32_vw<EPI_F64_ADD>(e, vw, o, m, r, sf, sd); break;
+        case EPI_OUT_F32: direct_run32_vw<EPI_OUT_F32>(e, vw, o, m, r, sf, sd); break;
+        case EPI_OUT_F64: direct_run32_vw<EPI_OUT_F64>(e, vw, o, m, r, sf, sd); break;
+        default: break;
+    }
+}
+
+// pdep64 computed by a whole warp: lane l deposits bits l and l + 32 of x,
+// then an OR reduction (every lane of the warp must call it).
+__device__ __forceinline__ uint64_t warp_pdep64(uint64_t x, uint64_t mask) {
+    const int ln = threadIdx.x & 31;
+    const uint32_t mlo = (uint32_t)mask, mhi = (uint32_t)(mask >> 32);
+    const int plo = __popc(mlo), ptot = plo + __popc(mhi);
+    uint64_t v = 0;
+#pragma unroll
+    for (int hw = 0; hw < 2; ++hw) {
+        const int idx = ln + 32 * hw;
+        if (idx < ptot && ((x >> idx) & 1)) {
+            const int pos = idx < plo ? (int)__fns(mlo, 0, idx + 1) : 32 + (int)__fns(mhi, 0, idx - plo + 1);
+            v |= 1ull << pos;
+        }
+    }
+    const uint32_t lo = __reduce_or_sync(0xffffffffu, (uint32_t)v);
+    const uint32_t hi = __reduce_or_sync(0xffffffffu, (uint32_t)(v >> 32));
+    return ((uint64_t)hi << 32) | lo;
 }
 
 }  // namespace tqc

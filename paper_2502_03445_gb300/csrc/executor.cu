@@ -15,6 +15,7 @@
 #include <mutex>
 #include <string>
 #include <tuple>
+#include <vector>
 
 #include "launch.h"
 #include "tqc_internal.h"
@@ -159,16 +160,55 @@ std::vector<int> tile_candidates(const StepPlan &st) {
 
 }  // namespace
 
-// Without autotuning: big tiles for big steps.  A long K loop (K >= 2^12)
-// over whole 128-row tiles takes the deep-K tensor-core form: 128 x 256
-// tiles when N allows (1.3-1.5x over 128 x 128 at K = 2^14 in every
-// precision), 128 x 128 ones only for split BF16 (slower than the staged
-// 128 x 128 form in plain BF16 and TF32).
-int default_step_tile(const StepPlan &st) {
+namespace {
+
+uint64_t host_pdep64(uint64_t src, uint64_t mask) {
+    uint64_t r = 0;
+    while (mask) {
+        const uint64_t low = mask & (~mask + 1);
+        if (src & 1) r |= low;
+        src >>= 1;
+        mask ^= low;
+    }
+    return r;
+}
+
+}  // namespace
+
+// Fraction of the bytes of the 32-byte sectors that one warp store of the
+// direct epilogue fills: lanes are 32 consecutive accumulator rows, each
+// storing its run of vw consecutive elements (the rule of umma.cu).
+double direct_store_efficiency(const EpiParams &e, int esize) {
+    const int vw = ((e.lowCc & 3u) == 3u && e.L >= 2) ? 4 : ((e.lowCc & 1u) && e.L >= 1 ? 2 : 1);
+    std::vector<uint64_t> sec;
+    for (uint32_t r = 0; r < 32; ++r) {
+        const uint64_t off = host_pdep64(host_pdep64(r, e.lowRc), e.tileMask);
+        for (int i = 0; i < vw; ++i) sec.push_back((off + (uint64_t)i) * (uint64_t)esize >> 5);
+    }
+    std::sort(sec.begin(), sec.end());
+    const size_t n = (size_t)(std::unique(sec.begin(), sec.end()) - sec.begin());
+    return 32.0 * vw * esize / (32.0 * (double)n);
+}
+
+// Without autotuning: big tiles for big steps.  The direct-epilogue
+// tensor-core form (*_DEEP) takes
+//  * steps with a long K loop (K >= 2^12) over whole 128-row tiles: 128 x 256
+//    tiles when N allows (1.3-1.5x over 128 x 128 at K = 2^14 in every
+//    precision), 128 x 128 ones only for split BF16;
+//  * steps whose direct warp stores fill whole 32-byte sectors (the result's
+//    lowest bits are column bits, then row bits, as in the Kronecker
+//    expansion of a final step), with 128 x 256 tiles (grid30's final step:
+//    1.08 ms against 1.50 ms for the staged epilogue).
+int default_step_tile(const StepPlan &st, int out_esize) {
     if (st.klass == KC_UMMA) {
-        const bool deep = st.kb >= DEEP_MIN_LOG2_K && st.mb >= 7;
+        const bool big = st.mb >= 7 && st.nb >= 7;
+        const bool deep = big && st.kb >= DEEP_MIN_LOG2_K;
         if (deep && st.nb >= 8) return UMMA_128x256_DEEP;
-        if (deep && st.nb == 7 && st.prec == TQC_PREC_BF16X3) return UMMA_128x128_DEEP;
+        if (deep && st.prec == TQC_PREC_BF16X3) return UMMA_128x128_DEEP;
+        if (big && st.nb >= 8) {
+            const EpiParams e = make_epi(st.maskR, st.maskC, st.mb, st.nb, TileShape{7, 6});
+            if (direct_store_efficiency(e, out_esize) >= 0.99) return UMMA_128x256_DEEP;
+        }
         return st.nb >= 7 ? UMMA_128x128 : UMMA_128x64;
     }
     return (st.mb >= 7 && st.nb >= 7) ? SIMT_128x128 : (st.mb >= 7 && st.nb >= 6 ? SIMT_128x64 : SIMT_64x64);
@@ -181,6 +221,14 @@ StepArgs exec_step_args(const Plan &p, const StepPlan &st, TileShape tile) {
     return step_args(p, p.tensors, st, p.d_ws, tile);
 }
 int exec_epi_mode(int storage) { return epi_mode_of(storage); }
+
+// Bytes per element the step's epilogue writes (a plane of a split-BF16
+// operand counts 2; a final step 4, its FP64 forms store at least as wide).
+int step_out_esize(const Plan &p, const StepPlan &st) {
+    if (st.final) return 4;
+    const int sg = p.tensors[st.c].storage;
+    return (sg == ST_BF16 || sg == ST_BF16X2) ? 2 : (sg == ST_F64 ? 8 : 4);
+}
 
 tqc_status exec_autotune(Plan *p, void *d_out, int out_dtype, cudaStream_t s) {
     const bool sliced = p->n_slices() > 1;
@@ -273,7 +321,7 @@ tqc_status exec_prepare(Plan *p) {
     TQC_CUDA(cudaMemset(p->d_zinfo, 0, 4 * sizeof(double) + 64), "memset");
     // tile choice without autotuning: big tiles for big steps
     for (auto &st : p->steps) {
-        st.tile = default_step_tile(st);
+        st.tile = default_step_tile(st, step_out_esize(*p, st));
     }
     p->ready = true;
     return TQC_OK;

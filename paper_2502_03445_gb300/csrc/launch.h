@@ -38,9 +38,12 @@ IngestArgs exec_leaf_args(const Plan &p, const TensorPlan &t, int j, const uint8
 StepArgs exec_step_args(const Plan &p, const StepPlan &st, TileShape tile);
 int exec_epi_mode(int storage);
 
-// Tile configuration of a step when it is not autotuned.
+// Tile configuration of a step when it is not autotuned (out_esize: bytes
+// per result element its epilogue writes).
 constexpr int DEEP_MIN_LOG2_K = 12;
-int default_step_tile(const StepPlan &st);
+int default_step_tile(const StepPlan &st, int out_esize);
+int step_out_esize(const Plan &p, const StepPlan &st);
+double direct_store_efficiency(const EpiParams &e, int esize);
 
 // Epilogue parameters for a step given its result masks and tile shape.
 EpiParams make_epi(uint64_t maskR, uint64_t maskC, int mb, int nb, TileShape t);

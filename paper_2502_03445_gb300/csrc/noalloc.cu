@@ -128,7 +128,7 @@ extern "C" tqc_status tqc_contract_noalloc(tqc_plan_t plan, const void *const *d
     p.profile = 0;
     net.device = dev;
     for (auto &st : p.steps) {  // the tile rule of the allocating path
-        st.tile = default_step_tile(st);
+        st.tile = default_step_tile(st, step_out_esize(p, st));
     }
     tqc_status st = exec_contract(&p, fixed_bits, d_out, out_dtype, nullptr, cuda_stream);
     // restore

@@ -380,6 +380,8 @@ void assign_layouts(Built &B, int m) {
     root.layout.modes.clear();
     for (int q : root.qubits) root.layout.modes.push_back({0, (int16_t)q});
     (void)m;
+    std::vector<int> producer(B.t.size(), -1);  // step that writes each tensor
+    for (size_t s = 0; s < B.s.size(); ++s) producer[(size_t)B.s[s].c] = (int)s;
     for (int s = (int)B.s.size() - 1; s >= 0; --s) {
         StepPlan &st = B.s[s];
         const Layout &LC = B.t[st.c].layout;
@@ -388,6 +390,33 @@ void assign_layouts(Built &B, int m) {
         std::vector<int> shared;
         std::set_intersection(A.cuts.begin(), A.cuts.end(), Bt.cuts.begin(), Bt.cuts.end(),
                               std::back_inserter(shared));
+        // The shared cuts form the K field, the lowest bits of both operands;
+        // their order is free as long as both operands agree.  Order it for
+        // the step that writes the row operand (else the column operand): one
+        // of its column-operand cuts first, then its row-operand cuts, so that
+        // its epilogue's warp stores cover whole sectors -- four consecutive
+        // columns per lane, consecutive rows in consecutive lanes.
+        {
+            const int t_in = producer[(size_t)st.a] >= 0 ? st.a : (producer[(size_t)st.b] >= 0 ? st.b : -1);
+            if (t_in >= 0) {
+                const StepPlan &ps = B.s[(size_t)producer[(size_t)t_in]];
+                const std::vector<int> &rc = B.t[ps.a].cuts, &cc = B.t[ps.b].cuts;
+                std::vector<int> cols, rows, rest;
+                for (int c : shared) {
+                    if (std::binary_search(cc.begin(), cc.end(), c)) cols.push_back(c);
+                    else if (std::binary_search(rc.begin(), rc.end(), c)) rows.push_back(c);
+                    else rest.push_back(c);
+                }
+                std::vector<int> ord;
+                if (!cols.empty()) ord.push_back(cols[0]);
+                ord.insert(ord.end(), rows.begin(), rows.end());
+                if (cols.size() > 1) ord.insert(ord.end(), cols.begin() + 1, cols.end());
+                ord.insert(ord.end(), rest.begin(), rest.end());
+                shared = ord;
+            }
+        }
+        std::vector<int> shared_sorted = shared;  // membership tests
+        std::sort(shared_sorted.begin(), shared_sorted.end());
         auto make = [&](TensorPlan &T, uint64_t *mask) {
             std::vector<std::pair<int, Mode>> outer;  // (position in LC, mode)
             for (int q : T.qubits) {
@@ -395,7 +424,7 @@ void assign_layouts(Built &B, int m) {
                 outer.push_back({LC.pos(md), md});
             }
             for (int c : T.cuts)
-                if (!std::binary_search(shared.begin(), shared.end(), c)) {
+                if (!std::binary_search(shared_sorted.begin(), shared_sorted.end(), c)) {
                     Mode md{1, (int16_t)c};
                     outer.push_back({LC.pos(md), md});
                 }

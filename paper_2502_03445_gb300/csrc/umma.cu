@@ -53,6 +53,7 @@ struct UmmaParams {
     int32_t k_blocks;
     int32_t rowmajor;  // staging orientation (pick_staging)
     int32_t gmode;     // gather mode of the write-out (pick_staging)
+    int32_t bres;      // B stays resident in shared memory (one k-block, one column tile; deep form)
     EpiParams epi;
     int *err;
 };
@@ -71,7 +72,9 @@ struct Cfg {
     static constexpr int PITCH_C = BM + 4;         // column-major staging pitch
     static constexpr int STG_FLOATS = BM * PITCH_R > SUB_N * PITCH_C ? BM * PITCH_R : SUB_N * PITCH_C;
     static constexpr int STG_BYTES = DEEP ? 0 : 2 * STG_FLOATS * 4;  // two buffers (ping-pong)
-    static constexpr int BAR_BYTES = 512;
+    static constexpr int BAR_BYTES = 1024;
+    static constexpr int RING = STAGES * STAGE_BYTES;      // bytes of the operand ring
+    static constexpr int MAXST = DEEP ? 16 : STAGES;        // barrier slots of the ring
     static constexpr int SMEM = 1024 + STAGES * STAGE_BYTES + STG_BYTES + (int)sizeof(EpiTables) + BAR_BYTES;
     static constexpr int TMEM_COLS = 2 * BN;
     static_assert(SMEM <= 232448, "shared memory per CTA");
@@ -190,24 +193,33 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t *stages = smem;
-    float *stg = (float *)(smem + C::STAGES * C::STAGE_BYTES);
-    EpiTables *tb = (EpiTables *)(smem + C::STAGES * C::STAGE_BYTES + C::STG_BYTES);
-    uint64_t *full = (uint64_t *)(smem + C::STAGES * C::STAGE_BYTES + C::STG_BYTES + sizeof(EpiTables));
-    uint64_t *empty = full + C::STAGES;
-    uint64_t *tfull = empty + C::STAGES;
+    float *stg = (float *)(smem + C::RING);
+    EpiTables *tb = (EpiTables *)(smem + C::RING + C::STG_BYTES);
+    uint64_t *full = (uint64_t *)(smem + C::RING + C::STG_BYTES + sizeof(EpiTables));
+    uint64_t *empty = full + C::MAXST;
+    uint64_t *tfull = empty + C::MAXST;
     uint64_t *tempty = tfull + 2;
     uint64_t *drain = tempty + 2;
-    uint32_t *tmem_slot = (uint32_t *)(drain + 1);
+    uint64_t *bfull = drain + 1;
+    uint32_t *tmem_slot = (uint32_t *)(bfull + 1);
+    // With B resident (deep form, a single k-block and column tile: B is the
+    // same for every tile) the ring holds A only and B sits at its end.
+    const bool bres = DEEP && P.bres;
+    const int sbytes = bres ? C::PLANES * C::A_BYTES : C::STAGE_BYTES;
+    const int nfit = (C::RING - C::PLANES * C::B_BYTES) / sbytes;
+    const int nst = bres ? (nfit < C::MAXST ? nfit : (int)C::MAXST) : (int)C::STAGES;
+    uint8_t *bsm = stages + C::RING - C::PLANES * C::B_BYTES;
     volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
     uint64_t *tile_base_slot = (uint64_t *)(tmem_slot + 2);  // epilogue: base offsets of two sub-tiles
     uint8_t *tb_pos = (uint8_t *)(tile_base_slot + 2);       // epilogue: tile-index bit positions
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
-        for (int s = 0; s < C::STAGES; ++s) {
+        for (int s = 0; s < nst; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
+        mbar_init(bfull, 1);
         for (int a = 0; a < 2; ++a) {
             mbar_init(&tfull[a], 1);
             mbar_init(&tempty[a], DEEP ? EPI_WARPS : STAGE_WARPS);
@@ -235,31 +247,44 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tB) : "memory");
             int64_t it = 0;
             bool ok = true;
+            if (bres) {  // the one B tile, loaded once
+                mbar_expect_tx(bfull, C::PLANES * C::B_BYTES);
+                tma_load_2d(bsm, &tB, 0, 0, bfull);
+                if (KIND == K_BF16X3) tma_load_2d(bsm + C::B_BYTES, &tBl, 0, 0, bfull);
+            }
             for (int64_t tile = blockIdx.x; ok && tile < P.n_tiles; tile += gridDim.x) {
                 const int rt = (int)(tile / P.col_tiles), ct = (int)(tile - (int64_t)rt * P.col_tiles);
                 for (int kb = 0; kb < P.k_blocks; ++kb, ++it) {
-                    const int s = (int)(it % C::STAGES);
-                    const uint32_t ph = (uint32_t)((it / C::STAGES) & 1);
+                    const int s = (int)(it % nst);
+                    const uint32_t ph = (uint32_t)((it / nst) & 1);
                     if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag)) {
                         ok = false;
                         break;
                     }
-                    uint8_t *sa = stages + s * C::STAGE_BYTES;
-                    mbar_expect_tx(&full[s], C::STAGE_BYTES);
+                    uint8_t *sa = stages + s * sbytes;
+                    mbar_expect_tx(&full[s], (uint32_t)sbytes);
                     tma_load_2d(sa, &tA, kb * C::BK, rt * BM, &full[s]);
-                    tma_load_2d(sa + C::A_BYTES, &tB, kb * C::BK, ct * BN, &full[s]);
-                    if (KIND == K_BF16X3) {
-                        tma_load_2d(sa + C::A_BYTES + C::B_BYTES, &tAl, kb * C::BK, rt * BM, &full[s]);
-                        tma_load_2d(sa + 2 * C::A_BYTES + C::B_BYTES, &tBl, kb * C::BK, ct * BN, &full[s]);
+                    if (bres) {
+                        if (KIND == K_BF16X3) tma_load_2d(sa + C::A_BYTES, &tAl, kb * C::BK, rt * BM, &full[s]);
+                    } else {
+                        tma_load_2d(sa + C::A_BYTES, &tB, kb * C::BK, ct * BN, &full[s]);
+                        if (KIND == K_BF16X3) {
+                            tma_load_2d(sa + C::A_BYTES + C::B_BYTES, &tAl, kb * C::BK, rt * BM, &full[s]);
+                            tma_load_2d(sa + 2 * C::A_BYTES + C::B_BYTES, &tBl, kb * C::BK, ct * BN, &full[s]);
+                        }
                     }
                 }
             }
             if (!ok) {
                 // drain: wait (bounded) for the copies still in flight in every stage
-                for (int64_t j = it > C::STAGES ? it - C::STAGES : 0; j < it; ++j) {
+                for (int64_t j = it > nst ? it - nst : 0; j < it; ++j) {
                     long long t0 = clock64();
-                    while (!mbar_try_wait(&full[j % C::STAGES], (uint32_t)((j / C::STAGES) & 1)) &&
-                           clock64() - t0 < WAIT_CYCLES) {
+                    while (!mbar_try_wait(&full[j % nst], (uint32_t)((j / nst) & 1)) && clock64() - t0 < WAIT_CYCLES) {
+                    }
+                }
+                if (bres) {
+                    long long t0 = clock64();
+                    while (!mbar_try_wait(bfull, 0) && clock64() - t0 < WAIT_CYCLES) {
                     }
                 }
             }
@@ -269,6 +294,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         if (lane == 0) {
             int64_t it = 0, lt = 0;
             bool ok = true;
+            if (bres) {
+                ok = mbar_wait(bfull, 0, abort_flag);
+                tc_fence_after();
+            }
             for (int64_t tile = blockIdx.x; ok && tile < P.n_tiles; tile += gridDim.x, ++lt) {
                 const int acc = (int)(lt & 1);
                 const uint32_t aph = (uint32_t)((lt >> 1) & 1);
@@ -279,17 +308,17 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 tc_fence_after();
                 const uint32_t d = tmem_base + (uint32_t)(acc * BN);
                 for (int kb = 0; kb < P.k_blocks; ++kb, ++it) {
-                    const int s = (int)(it % C::STAGES);
-                    const uint32_t ph = (uint32_t)((it / C::STAGES) & 1);
+                    const int s = (int)(it % nst);
+                    const uint32_t ph = (uint32_t)((it / nst) & 1);
                     if (!mbar_wait(&full[s], ph, abort_flag)) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t a0 = smem_u32(stages + s * C::STAGE_BYTES);
-                    const uint32_t b0 = a0 + C::A_BYTES;
-                    const uint32_t al = b0 + C::B_BYTES;
-                    const uint32_t bl = al + C::A_BYTES;
+                    const uint32_t a0 = smem_u32(stages + s * sbytes);
+                    const uint32_t b0 = bres ? smem_u32(bsm) : a0 + C::A_BYTES;
+                    const uint32_t al = bres ? a0 + C::A_BYTES : b0 + C::B_BYTES;
+                    const uint32_t bl = bres ? b0 + C::B_BYTES : al + C::A_BYTES;
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {  // four 32-byte K slices of the 128-byte atom
                         const uint64_t da = umma_desc(a0 + 32 * k), db = umma_desc(b0 + 32 * k);
@@ -313,23 +342,29 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         // ------------------------------------------------ direct epilogue
         // Warp (lane group g, quarter q) owns accumulator rows 32g..32g+31
         // and the 32-column chunks q, q + 4, ...; it frees the accumulator as
-        // soon as its loads land and then stores every value to its place in
-        // the result layout: offset = tile base + G_row[r] + G_col[c], both
-        // parts deposits of the tile-local row / column bits.
+        // soon as its loads land and then stores every value straight to its
+        // place in the result layout: tile base + row part + column part,
+        // each a deposit of the tile-local index bits into result bits.
         constexpr int CH = BN / 128;     // chunks per warp
         constexpr int SUBS = BN / C::SUB_N;
         const int q = (warp - 2) >> 2;
         const int lane_grp = warp & 3;
         const int row = lane_grp * 32 + lane;
-        const int etid = threadIdx.x - 64;
-        uint64_t *gcol = (uint64_t *)tb;  // G_col of the 64 columns of a sub-tile
-        if (etid < C::SUB_N) gcol[etid] = pdep64((uint64_t)pdep32((uint32_t)etid, e.lowCc), e.tileMask);
-        asm volatile("bar.sync 1, %0;" ::"n"(EPI_THREADS) : "memory");
         const uint64_t grow = pdep64((uint64_t)pdep32((uint32_t)row, e.lowRc), e.tileMask);
-        const double sc = (e.mode == EPI_OUT_F32 || e.mode == EPI_OUT_F64) ? e.zinfo[1] : 1.0;
-        // four consecutive columns are four consecutive elements when the two
-        // lowest tile bits are column bits at result bits 0 and 1
-        const bool vec4 = (e.lowCc & 3u) == 3u && e.L >= 2;
+        const uint64_t colmask = pdep64((uint64_t)e.lowCc, e.tileMask);  // result bits of the column index
+        // runs of 2^w columns are contiguous when the w lowest tile bits are
+        // column bits at result bits 0..w-1
+        const int vw = ((e.lowCc & 3u) == 3u && e.L >= 2) ? 4 : ((e.lowCc & 1u) && e.L >= 1 ? 2 : 1);
+        const uint64_t mstep = vw == 4 ? colmask & (colmask - 1) & ((colmask & (colmask - 1)) - 1)
+                                       : (vw == 2 ? colmask & (colmask - 1) : colmask);
+        uint64_t coff[CH];  // column part of each chunk's first column, sub-tile index included
+#pragma unroll
+        for (int c = 0; c < CH; ++c) {
+            const int col0 = (q + 4 * c) * 32;
+            coff[c] = pdep64((uint64_t)(col0 % C::SUB_N), colmask) | pdep64((uint64_t)(col0 / C::SUB_N), e.highC);
+        }
+        const double sd = (e.mode == EPI_OUT_F32 || e.mode == EPI_OUT_F64) ? e.zinfo[1] : 1.0;
+        const float sf = (float)sd;
         int64_t lt = 0;
         for (int64_t tile = blockIdx.x; tile < P.n_tiles; tile += gridDim.x, ++lt) {
             const int acc = (int)(lt & 1);
@@ -337,34 +372,22 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             __syncwarp();
             if (*abort_flag) break;
             tc_fence_after();
-            uint32_t r[CH][32];
-#pragma unroll
-            for (int c = 0; c < CH; ++c)
-                tmem_ld32(tmem_base + ((uint32_t)(lane_grp * 32) << 16) + (uint32_t)(acc * BN + (q + 4 * c) * 32), r[c]);
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&tempty[acc]);
             const uint64_t rt = (uint64_t)(tile / P.col_tiles);
             const uint64_t ct = (uint64_t)(tile - (int64_t)rt * P.col_tiles);
+            // sub-tile column index ct * SUBS + h: the h bits are the lowest bits of highC (in coff)
+            const uint64_t base = warp_pdep64(rt, e.highR) | warp_pdep64(ct * SUBS, e.highC);
+            // one 32-column chunk at a time (registers); the accumulator is
+            // freed once the last chunk has been loaded
 #pragma unroll
             for (int c = 0; c < CH; ++c) {
-                const int col0 = (q + 4 * c) * 32;
-                const uint64_t o = tile_base(e, rt, ct * SUBS + (uint64_t)(col0 / C::SUB_N)) + grow;
-                const uint64_t *gc = gcol + (col0 % C::SUB_N);
-                if (vec4) {
-#pragma unroll
-                    for (int j = 0; j < 32; j += 4) {
-                        const float v[4] = {__uint_as_float(r[c][j]), __uint_as_float(r[c][j + 1]),
-                                            __uint_as_float(r[c][j + 2]), __uint_as_float(r[c][j + 3])};
-                        store_run_f32(e, o + gc[j], v, 4, sc);
-                    }
-                } else {
-#pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        const float v = __uint_as_float(r[c][j]);
-                        store_run_f32(e, o + gc[j], &v, 1, sc);
-                    }
+                uint32_t r[32];
+                tmem_ld32(tmem_base + ((uint32_t)(lane_grp * 32) << 16) + (uint32_t)(acc * BN + (q + 4 * c) * 32), r);
+                if (c == CH - 1) {
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&tempty[acc]);
                 }
+                direct_run32_any(e, vw, base + grow + coff[c], mstep, r, sf, sd);
             }
         }
     } else {
@@ -594,6 +617,7 @@ cudaError_t launch_kind(const StepArgs &a, int *d_err, cudaStream_t s) {
     p.col_tiles = a.nb >= lbn ? (int64_t)1 << (a.nb - lbn) : 1;
     p.n_tiles = row_tiles * p.col_tiles;
     p.k_blocks = (int)(K / C::BK);
+    p.bres = DEEP && p.k_blocks == 1 && p.col_tiles == 1;
     const StagePick pk = pick_staging(a.epi.lowRc, a.epi.lowCc);
     p.rowmajor = pk.rowmajor;
     p.gmode = pk.gmode;

@@ -274,6 +274,39 @@ def test_tensor_core_deep_k_sliced_f64():
     check_fp32(got, want)
 
 
+def kron_final_network(seed, cuts):
+    """Two nodes whose final step writes the bin in qubit order with a
+    column qubit at bit 0 and seven row qubits above it: the direct
+    epilogue's warp stores fill whole sectors, so a 128 x 256 direct tile
+    is the default even at small K."""
+    outs = [[1, 2, 3, 4, 5, 6, 7, 9, 11], [0, 8, 10, 12, 13, 14, 15, 16]]
+    return tensors.pseudo_physical_network(17, [(0, 1)] * cuts, outs, seed)
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "bf16", "tf32"])
+def test_final_step_direct_epilogue(prec):
+    net = kron_final_network(1500, 3)
+    want = oracle.recon_bin(net)
+    got, z, d = run(net, precision=prec)
+    st = d["steps"][-1]
+    assert st["log2_k"] == 6 and st["tile"] == UMMA_128x256_DEEP, st
+    if prec == "bf16x3":
+        check_fp32(got, want)
+    else:
+        check_tc(prec, got, net, d, want)
+
+
+def test_final_step_direct_epilogue_sliced_and_f64():
+    net = kron_final_network(1501, 4)
+    want = oracle.recon_bin(net)
+    got, z, d = run(net, precision="bf16x3", sliced=[1], out_f64=True)       # FP64 slice sum
+    assert d["sliced"] == [1] and d["steps"][-1]["tile"] == UMMA_128x256_DEEP
+    check_fp32(got, want)
+    got, z, d = run(net, precision="bf16x3", out_f64=True)                    # scaled FP64 output
+    assert d["steps"][-1]["tile"] == UMMA_128x256_DEEP
+    check_fp32(got, want)
+
+
 def abs_mass(net):
     """sum_x of the reconstruction with |T_j| in place of T_j: the sum of
     the absolute values of every term, which bounds rounding errors."""
