@@ -10,6 +10,7 @@ in HBM.  Metric: reconstructed probabilities per second, for the chosen form
 CUDA-core form.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+  python bench.py --workload qaoa48|grid64   (tensor-bound bins, one JSON line)
 
 Under torchrun each rank reconstructs its own network instance (weak
 scaling, no collective on the data path); rank 0 prints one JSON line.
@@ -52,6 +53,10 @@ def parse():
                     help="instead: time the batched persistent launch over this many networks")
     ap.add_argument("--batch-n-lo", type=int, default=16)
     ap.add_argument("--batch-n-hi", type=int, default=24)
+    ap.add_argument("--workload", default="grid30", choices=["grid30", "qaoa48", "grid64"],
+                    help="qaoa48 / grid64: time one bin of 2^24 states of the tensor-bound networks instead")
+    ap.add_argument("--mem-budget-gb", type=float, default=32.0,
+                    help="device memory budget of the qaoa48 / grid64 plans (forces slicing)")
     return ap.parse_args()
 
 
@@ -293,6 +298,72 @@ def run_batch(args):
     return 0
 
 
+def tensor_peak(prec, bf16):
+    """(peak in algorithmic TFLOP/s, how it is derived) of a tensor-core step."""
+    if prec == "bf16x3":
+        return bf16 / 3.0, "measured bf16 burst / 3 (split BF16 issues three MMAs per product)"
+    if prec == "tf32":
+        return bf16 * 1.1 / 2.25, "measured bf16 burst x 1.1/2.25 (nominal TF32/BF16 ratio)"
+    return bf16, "measured bf16 burst"
+
+
+def run_workload(args):
+    """One 2^24-state bin of the 48-qubit QAOA network or of the 64-qubit
+    grid shape, sliced to the memory budget: these plans end in tensor-bound
+    steps (K = 4^7..4^9 after slicing), so the roofline is the tensor pipe."""
+    import torch
+    from gen import workloads
+    from paper_2502_03445_gb300 import tqc
+    import oracle
+    torch.cuda.set_device(0)
+    net = workloads.qaoa48(0) if args.workload == "qaoa48" else workloads.grid64_bin(0, 0)
+    h = tqc.Network(net)
+    plan = tqc.Plan(h, precision=args.precision, mem_budget=int(args.mem_budget_gb * (1 << 30)))
+    out = torch.empty(plan.out_elems, dtype=torch.float32, device="cuda")
+    ms = time_plan(torch, plan, out, args.steps, args.warmup, profile=True)
+    desc = plan.describe()
+    info = plan.info()
+    step_ms = [plan.step_time(i)[0] for i in range(len(desc["steps"]))]
+    plan.profile(False)
+    top = int(np.argmax(step_ms))
+    st = desc["steps"][top]
+    alg = 2.0 * 2 ** (st["log2_m"] + st["log2_n"] + st["log2_k"])
+    _, bf16, _, peak_kind = peaks()
+    pk, how = tensor_peak(st["prec"], bf16)
+    achieved = alg / (step_ms[top] / 1e3) / 1e12
+    roof = {"bound": "tensor", "achieved": achieved, "peak": pk, "unit": "TFLOP/s", "frac": achieved / pk,
+            "traffic": None, "peak_kind": f"{peak_kind}: {how}",
+            "kernel": f"umma_step (step {top}: log2 M,N,K = {st['log2_m']},{st['log2_n']},{st['log2_k']}, "
+                      f"tile {st['tile']})",
+            "algorithmic_flops_per_launch": alg, "mean_launch_ms": step_ms[top], "step_ms": step_ms,
+            "tensor_pipe_issue_frac_of_bf16": achieved * (3 if st["prec"] == "bf16x3" else 1) / bf16}
+    # sampled check and CPU baseline: oracle B, one state at a time
+    rng = np.random.Generator(np.random.PCG64(5))
+    states = [int(x) for x in rng.integers(0, 1 << net.n_qubits, size=4)]
+    t0 = time.perf_counter()
+    want = oracle.recon_states_elim(net, states)
+    t_cpu = time.perf_counter() - t0
+    z = oracle.total_mass(net)
+    got = out.double().cpu().numpy()[states]
+    line = {"metric": METRIC, "value": plan.out_elems / (ms / 1e3), "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": desc["precision"], "data": "synthetic",
+            "config": {"workload": f"{args.workload}: bin of 2^24 states, {net.n_cuts} cuts, "
+                                   f"{len(net.nodes)} subcircuits, node tensors drawn bin-restricted",
+                       "slices": info["n_slices"], "sliced": desc["sliced"],
+                       "plan": [[s_["log2_m"], s_["log2_n"], s_["log2_k"], s_["class"], s_["tile"]]
+                                for s_ in desc["steps"]],
+                       "flops_per_step": info["flops"], "mem_budget_gb": args.mem_budget_gb},
+            "tflops_per_step": info["flops"] / (ms / 1e3) / 1e12,
+            "roofline": roof, "gpu_launches": desc["launches_per_contract"] * args.steps,
+            "sampled_max_abs_err": float(np.abs(got - want / z).max()),
+            "cpu_baseline": {"value": len(states) / t_cpu, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": f"{len(states)} states, oracle B (FP64 pairwise elimination per state; "
+                                       f"numpy tensordot, BLAS threads up to the host's cores)"}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def time_plan(torch, plan, out, steps, warmup, profile=False):
     for _ in range(warmup):
         plan.contract(out)
@@ -314,6 +385,8 @@ def main():
         return run_reference(args)
     if args.batch > 0:
         return run_batch(args)
+    if args.workload != "grid30":
+        return run_workload(args)
     ws, rank, local = dist_env()
     import torch
     import torch.distributed as dist
