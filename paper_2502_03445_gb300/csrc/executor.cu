@@ -197,17 +197,18 @@ double direct_store_efficiency(const EpiParams &e, int esize) {
 //    precision), 128 x 128 ones only for split BF16;
 //  * steps whose direct warp stores fill whole 32-byte sectors (the result's
 //    lowest bits are column bits, then row bits, as in the Kronecker
-//    expansion of a final step), with 128 x 256 tiles (grid30's final step:
-//    1.08 ms against 1.50 ms for the staged epilogue).
+//    expansion of a final step), with 128 x 256 tiles when N allows (grid30's
+//    final step: 0.92 ms against 1.50 ms staged), else 128 x 128 (grid30's
+//    step 1, N = 128: 0.48 ms against 0.56 ms, the autotuner's choice).
 int default_step_tile(const StepPlan &st, int out_esize) {
     if (st.klass == KC_UMMA) {
         const bool big = st.mb >= 7 && st.nb >= 7;
         const bool deep = big && st.kb >= DEEP_MIN_LOG2_K;
         if (deep && st.nb >= 8) return UMMA_128x256_DEEP;
-        if (deep && st.prec == TQC_PREC_BF16X3) return UMMA_128x128_DEEP;
-        if (big && st.nb >= 8) {
+        if (deep) return st.prec == TQC_PREC_BF16X3 ? UMMA_128x128_DEEP : UMMA_128x128;
+        if (big) {
             const EpiParams e = make_epi(st.maskR, st.maskC, st.mb, st.nb, TileShape{7, 6});
-            if (direct_store_efficiency(e, out_esize) >= 0.99) return UMMA_128x256_DEEP;
+            if (direct_store_efficiency(e, out_esize) >= 0.99) return st.nb >= 8 ? UMMA_128x256_DEEP : UMMA_128x128_DEEP;
         }
         return st.nb >= 7 ? UMMA_128x128 : UMMA_128x64;
     }

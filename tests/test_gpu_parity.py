@@ -274,22 +274,26 @@ def test_tensor_core_deep_k_sliced_f64():
     check_fp32(got, want)
 
 
-def kron_final_network(seed, cuts):
+def kron_final_network(seed, cuts, fb=8):
     """Two nodes whose final step writes the bin in qubit order with a
     column qubit at bit 0 and seven row qubits above it: the direct
-    epilogue's warp stores fill whole sectors, so a 128 x 256 direct tile
-    is the default even at small K."""
+    epilogue's warp stores fill whole sectors, so a direct tile (128 x 256,
+    or 128 x 128 when N = 128) is the default even at small K."""
     outs = [[1, 2, 3, 4, 5, 6, 7, 9, 11], [0, 8, 10, 12, 13, 14, 15, 16]]
+    if fb == 7:
+        outs = [[1, 2, 3, 4, 5, 6, 7, 9, 11, 16], [0, 8, 10, 12, 13, 14, 15]]
     return tensors.pseudo_physical_network(17, [(0, 1)] * cuts, outs, seed)
 
 
+@pytest.mark.parametrize("fb", [8, 7])
 @pytest.mark.parametrize("prec", ["bf16x3", "bf16", "tf32"])
-def test_final_step_direct_epilogue(prec):
-    net = kron_final_network(1500, 3)
+def test_final_step_direct_epilogue(prec, fb):
+    net = kron_final_network(1500 + fb, 3, fb)
     want = oracle.recon_bin(net)
     got, z, d = run(net, precision=prec)
     st = d["steps"][-1]
-    assert st["log2_k"] == 6 and st["tile"] == UMMA_128x256_DEEP, st
+    assert st["log2_n"] == fb and st["log2_k"] == 6, st
+    assert st["tile"] == (UMMA_128x256_DEEP if fb == 8 else UMMA_128x128_DEEP), st
     if prec == "bf16x3":
         check_fp32(got, want)
     else:
