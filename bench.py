@@ -204,35 +204,6 @@ def run_reference(args):
     return 0
 
 
-def batch_networks(count, n_lo, n_hi, seed0=3000, max_node_elems=1 << 24):
-    """The batched workload's recipe: n ~ U{n_lo..n_hi}, m ~ U{2..8},
-    |E| ~ U{max(2, m-1)..12}, widths up to n; networks whose largest
-    subcircuit tensor exceeds max_node_elems are redrawn (count returned)."""
-    from gen import tensors
-    rng = np.random.Generator(np.random.PCG64(seed0))
-    nets, redraws = [], 0
-    while len(nets) < count:
-        n = int(rng.integers(n_lo, n_hi + 1))
-        m = int(rng.integers(2, 9))
-        cuts = int(rng.integers(max(2, m - 1), 13))
-        seed = int(rng.integers(1 << 30))
-        try:
-            shape_rng = np.random.Generator(np.random.PCG64(seed))
-            edges, outs = tensors.sample_shape(n, m, cuts, n, shape_rng, max_node_cuts=10)
-        except RuntimeError:
-            redraws += 1
-            continue
-        deg = [0] * m
-        for a, b in edges:
-            deg[a] += 1
-            deg[b] += 1
-        if max((4 ** deg[j]) << len(outs[j]) for j in range(m)) > max_node_elems:
-            redraws += 1
-            continue
-        nets.append(tensors.random_shape_network(n, m, cuts, n, seed, max_node_cuts=10))
-    return nets, redraws
-
-
 def run_batch(args):
     """Batched persistent launch: `--batch` independent networks of uneven
     sizes reconstructed by one tqc_contract_batch launch replayed from a CUDA
@@ -240,7 +211,8 @@ def run_batch(args):
     import torch
     from paper_2502_03445_gb300 import tqc
     torch.cuda.set_device(0)
-    nets, redraws = batch_networks(args.batch, args.batch_n_lo, args.batch_n_hi)
+    from gen import workloads
+    nets, redraws = workloads.batch_recipe(args.batch, args.batch_n_lo, args.batch_n_hi)
     hs, plans, outs = [], [], []
     for net in nets:
         h = tqc.Network(net, dtype=tqc.F32)

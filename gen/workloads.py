@@ -16,6 +16,8 @@
 * ``grid64``: the shape of a 64-qubit (8x8) grid cut into 6 subcircuits of
   width <= 20 with 27 cuts; a stream of bins of 2^24 states (qubits 0-23
   free), each bin's node tensors drawn already restricted with its own seed.
+* ``batch_recipe``: 256 independent networks of uneven sizes (n 16-28,
+  2-8 subcircuits, 2-12 cuts) for the batched persistent launch.
 * ``small_random``: tiny exact cut circuits for parity and oracle pins.
 """
 from __future__ import annotations
@@ -105,6 +107,36 @@ def grid64_bin(instance: int = 0, bin_index: int = 0, free_qubits=tuple(range(24
                                           seed=1000 * 5 + 100 * (instance + 1) + bin_index,
                                           meta={"workload": "grid64", "bin": bin_index, "edges": edges,
                                                 "circuit": "shape of 8x8 grid, 6 subcircuits, width <= 20, 27 cuts"})
+
+
+def batch_recipe(count: int = 256, n_lo: int = 16, n_hi: int = 28, seed0: int = 3000,
+                 max_node_elems: int = 1 << 24):
+    """The batched workload: ``count`` independent networks with n ~ U{n_lo..n_hi},
+    m ~ U{2..8}, |E| ~ U{max(2, m-1)..12}, widths up to n, i.i.d. Gaussian
+    FP32-valued tensors.  Networks whose largest subcircuit tensor exceeds
+    ``max_node_elems`` are redrawn.  Returns (networks, redraw count)."""
+    rng = np.random.Generator(np.random.PCG64(seed0))
+    nets, redraws = [], 0
+    while len(nets) < count:
+        n = int(rng.integers(n_lo, n_hi + 1))
+        m = int(rng.integers(2, 9))
+        cuts = int(rng.integers(max(2, m - 1), 13))
+        seed = int(rng.integers(1 << 30))
+        try:
+            shape_rng = np.random.Generator(np.random.PCG64(seed))
+            edges, outs = tensors.sample_shape(n, m, cuts, n, shape_rng, max_node_cuts=10)
+        except RuntimeError:
+            redraws += 1
+            continue
+        deg = [0] * m
+        for a, b in edges:
+            deg[a] += 1
+            deg[b] += 1
+        if max((4 ** deg[j]) << len(outs[j]) for j in range(m)) > max_node_elems:
+            redraws += 1
+            continue
+        nets.append(tensors.random_shape_network(n, m, cuts, n, seed, max_node_cuts=10))
+    return nets, redraws
 
 
 def random_cut_circuit(seed: int, n: int, depth: int, n_sub: int, family: str = "line"):

@@ -4,7 +4,7 @@ import numpy as np
 import pytest
 
 import oracle
-from gen import Network, Node, tensors
+from gen import Network, Node, tensors, workloads
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -109,3 +109,53 @@ def test_batch_rejects_sliced_plans():
     with pytest.raises(tqc.TqcError) as ei:
         tqc.contract_batch([p], [o])
     assert ei.value.status == tqc.ERR_UNSUPPORTED
+
+
+def test_batch_full_recipe_sampled():
+    """The batched workload at full size: 256 networks (n 16-28, 2-8
+    subcircuits, 2-12 cuts, 1.0e10 outputs), one persistent launch replayed
+    from a CUDA graph; four sampled states per network against oracle A.
+    Raw probabilities (no renormalisation: the Gaussian tensors' total mass
+    can be near zero), errors measured against each network's mean absolute
+    term mass per state (the reconstruction with |T_j|), bound
+    n_steps * 2^-12 of it (split BF16 or FP32 products, FP32 accumulation)."""
+    nets, _ = workloads.batch_recipe(256)
+    hs, plans, outs = [], [], []
+    for net in nets:
+        h = tqc.Network(net, dtype=tqc.F32)
+        p = tqc.Plan(h, precision="auto", flags=tqc.FLAG_NO_RENORM)
+        o = torch.empty(p.out_elems, dtype=torch.float32, device="cuda")
+        p.contract(o)
+        hs.append(h)
+        plans.append(p)
+        outs.append(torch.full_like(o, float("nan")))
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        tqc.contract_batch(plans, outs, stream=s)
+    s.synchronize()
+    for o in outs:
+        o.fill_(float("nan"))
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        tqc.contract_batch(plans, outs, stream=s)
+    g.replay()
+    torch.cuda.synchronize()
+    tqc.batch_status()
+    rng = np.random.Generator(np.random.PCG64(77))
+    worst = 0.0
+    for net, p, o in zip(nets, plans, outs):
+        idx = sorted(set(int(i) for i in rng.integers(0, 1 << net.n_qubits, size=4)))
+        want = oracle.recon_states(net, idx)
+        got = o[torch.tensor(idx, device="cuda")].double().cpu().numpy()
+        a = Network(net.n_qubits, net.n_cuts,
+                    [Node(nd.out_qubits, nd.cut_ids, nd.cut_role, np.abs(nd.data)) for nd in net.nodes])
+        scale = oracle.total_mass(a) / float(1 << net.n_qubits)
+        n_steps = max(len(p.describe()["steps"]), 1)
+        rel = float(np.abs(got - want).max()) / (n_steps * 2.0 ** -12 * scale)
+        worst = max(worst, rel)
+        assert rel <= 1.0, (net.n_qubits, net.n_cuts, rel)
+    print(f"batch256: worst error / bound {worst:.3e}")
+    for p in plans:
+        p.close()
+    for h in hs:
+        h.close()

@@ -5,6 +5,8 @@
   slicing: the final step is a tensor-core GEMM with K = 4^9..4^11.
 * The 64-qubit grid shape (6 subcircuits, width <= 20, 27 cuts), a stream of
   bins of 2^24 states: one plan, new node tensors uploaded per bin.
+* The bench workload itself: the 30-qubit grid shape, the full 2^30 bin, in
+  the launch configuration bench.py times (checked with oracle A).
 
 The oracle cannot produce 2^24 probabilities at these cut counts, so each
 test checks (i) sampled states one by one with oracle B, and (ii) properties
@@ -124,5 +126,33 @@ def test_grid64_bin_stream():
                 h.upload(j, nd.data)
         got, z = contract_raw(p)
         check_result(net, got, z, d, sample(24, 2 if b < 2 else 0, 50 + b) or [0], f"grid64/bin{b}")
+    p.close()
+    h.close()
+
+
+@pytest.mark.parametrize("prec", ["auto", "fp32"])
+def test_grid30_full_bin_sampled(prec):
+    """bench.py's workload and launch configuration: every qubit free, the
+    default plan (split-BF16 tensor-core steps with the direct and staged
+    epilogues, or the plain FP32 form), renormalised FP32 output."""
+    net = workloads.grid30(0)
+    h = tqc.Network(net)
+    p = tqc.Plan(h, precision=prec)
+    out = torch.empty(p.out_elems, dtype=torch.float32, device="cuda")
+    z = p.contract(out, want_z=True)
+    torch.cuda.synchronize()
+    d = p.describe()
+    if prec == "auto":
+        assert [s_["class"] for s_ in d["steps"]] == ["tcgen05"] * 3
+    idx = sample(30, 256, 9)
+    z_or = oracle.total_mass(net)
+    want = oracle.recon_states(net, idx) / z_or
+    got = out[torch.tensor(idx, device="cuda")].double().cpu().numpy()
+    err = np.abs(got - want)
+    print(f"grid30/{prec}: tiles {[s_['tile'] for s_ in d['steps']]} max|err| {err.max():.3e} "
+          f"max|P| {np.abs(want).max():.3e} Z {z:.12f} (oracle {z_or:.12f})")
+    assert abs(z - z_or) <= 1e-9
+    assert err.max() <= FP32_ATOL
+    assert err.max() <= 1e-4 * np.abs(want).max()
     p.close()
     h.close()
