@@ -57,6 +57,11 @@ def parse():
                     help="qaoa48 / grid64: time one bin of 2^24 states of the tensor-bound networks instead")
     ap.add_argument("--mem-budget-gb", type=float, default=32.0,
                     help="device memory budget of the qaoa48 / grid64 plans (forces slicing)")
+    ap.add_argument("--planner-eval", action="store_true",
+                    help="instead: learned vs greedy vs exhaustive planner on 48-qubit QAOA bins")
+    ap.add_argument("--pe-train", type=int, default=40)
+    ap.add_argument("--pe-test", type=int, default=12)
+    ap.add_argument("--pe-candidates", type=int, default=6)
     return ap.parse_args()
 
 
@@ -336,6 +341,85 @@ def run_workload(args):
     return 0
 
 
+def run_planner_eval(args):
+    """The learned planner on its configuration: 48-qubit QAOA p=1 bins of
+    2^24 states (16-24 cuts, subcircuits <= 16 qubits, sliced to the memory
+    budget).  The MLP cost model (3 x 128) is trained on the GPU on the
+    planner's own timings of every candidate plan of the training instances;
+    on held-out instances the plans chosen by the greedy, exhaustive (DP on
+    the analytic model) and learned planners are timed against the fastest
+    candidate."""
+    import math
+    import torch
+    from gen import workloads
+    from paper_2502_03445_gb300 import costmodel, tqc
+    torch.cuda.set_device(0)
+    budget = int(args.mem_budget_gb * (1 << 30))
+    t0 = time.perf_counter()
+    train, test, skipped = [], [], []
+    k = 0
+    while len(test) < args.pe_test:
+        try:
+            net = workloads.qaoa48_timing(k)
+        except RuntimeError:      # no 16-24 cut partition within the width cap
+            skipped.append(k)
+            k += 1
+            continue
+        h = tqc.Network(net, dtype=tqc.F32)
+        recs = costmodel.collect(h, precision=args.precision, max_candidates=args.pe_candidates, reps=2,
+                                 mem_budget=budget)
+        if k - len(skipped) < args.pe_train:
+            train.extend(recs)
+        else:
+            test.append((k, recs))
+        h.close()
+        k += 1
+    t_collect = time.perf_counter() - t0
+    X, y = costmodel.dataset(train)
+    cm = tqc.CostModel(X.shape[1], seed=0)
+    t1 = time.perf_counter()
+    cm.train(X, y, epochs=400, batch=32, lr=1e-3, seed=1)
+    t_train = time.perf_counter() - t1
+    path = os.path.join(tempfile.mkdtemp(), "costmodel.bin")
+    cm.save(path)
+    out = torch.empty(1 << 24, dtype=torch.float32, device="cuda")
+    ratios = {"greedy": [], "exhaustive": [], "learned": []}
+    err_mlp, err_ana = [], []
+    for k, recs in test:
+        yt = np.log([r["seconds"] for r in recs])
+        pred = costmodel.predicted_log_seconds(cm, recs)
+        err_mlp.append(float(np.mean(np.abs(pred - yt))))
+        err_ana.append(float(np.mean(np.abs(np.log([r["predicted_s"] for r in recs]) - yt))))
+        best = min(r["seconds"] for r in recs)
+        h = tqc.Network(workloads.qaoa48_timing(k), dtype=tqc.F32)
+        for name, pl in (("greedy", tqc.PLANNER_GREEDY), ("exhaustive", tqc.PLANNER_EXHAUSTIVE),
+                         ("learned", tqc.PLANNER_LEARNED)):
+            p = tqc.Plan(h, precision=args.precision, planner=pl, mem_budget=budget,
+                         costmodel_path=path if pl == tqc.PLANNER_LEARNED else None)
+            assert pl != tqc.PLANNER_LEARNED or p.describe()["planner"] == "learned"
+            secs = costmodel.time_plan(p, out, reps=2)
+            ratios[name].append(secs / best)
+            p.close()
+        h.close()
+    cm.close()
+    gm = {k: float(math.exp(np.mean(np.log(v)))) for k, v in ratios.items()}
+    line = {"metric": "plan time / fastest candidate (geometric mean over held-out instances)",
+            "value": gm["learned"], "unit": "ratio", "n_gpus": 1, "higher_is_better": False,
+            "data": "synthetic (QAOA-48 shapes, Gaussian values: timing only)",
+            "config": {"workload": "48-qubit QAOA p=1 on 3-regular graphs, 5-6 subcircuits <= 16 qubits, "
+                                   "16-24 cuts, bin of 2^24 states", "train_instances": args.pe_train,
+                       "test_instances": args.pe_test, "candidates_per_instance": args.pe_candidates,
+                       "mem_budget_gb": args.mem_budget_gb, "precision": args.precision,
+                       "model": "MLP 32-128-128-128-1 (ReLU), MSE on log(measured / analytic seconds), own GPU kernels"},
+            "planner_time_over_best": gm,
+            "learned_vs_greedy_speedup": gm["greedy"] / gm["learned"],
+            "held_out_mean_abs_log_error": {"mlp": float(np.mean(err_mlp)), "analytic": float(np.mean(err_ana))},
+            "train_records": len(train), "skipped_instances": skipped, "collect_s": t_collect,
+            "train_s": t_train}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def time_plan(torch, plan, out, steps, warmup, profile=False):
     for _ in range(warmup):
         plan.contract(out)
@@ -357,6 +441,8 @@ def main():
         return run_reference(args)
     if args.batch > 0:
         return run_batch(args)
+    if args.planner_eval:
+        return run_planner_eval(args)
     if args.workload != "grid30":
         return run_workload(args)
     ws, rank, local = dist_env()

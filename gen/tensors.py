@@ -253,6 +253,29 @@ def bin_restricted_network(n_qubits: int, edges, outs, free_qubits, seed: int, m
     return net
 
 
+def restricted_shape_network(n_qubits: int, edges, outs, free_qubits, seed: int) -> Network:
+    """The shape of ``bin_restricted_network`` with i.i.d. N(0,1) FP32-valued
+    entries: fast to draw where only timing matters (planner training)."""
+    free = sorted(int(q) for q in free_qubits)
+    rank = {q: i for i, q in enumerate(free)}
+    rng = np.random.Generator(np.random.PCG64(seed))
+    m = len(outs)
+    cuts = [[] for _ in range(m)]
+    for cid, (a, b) in enumerate(edges):
+        cuts[a].append((cid, 0))
+        cuts[b].append((cid, 1))
+    nodes = []
+    for j in range(m):
+        cl = sorted(cuts[j])
+        f = sorted(rank[q] for q in outs[j] if q in rank)
+        size = (4 ** len(cl)) << len(f)
+        nodes.append(Node(f, [c for c, _ in cl], [r for _, r in cl],
+                          rng.standard_normal(size, dtype=np.float32).astype(np.float64)))
+    net = Network(len(free), len(edges), nodes, {"kind": "gaussian-restricted", "seed": seed, "free_qubits": free})
+    net.check()
+    return net
+
+
 def shape_matched_network(n_qubits: int, m: int, n_cuts: int, w_max: int, seed: int,
                           max_node_cuts: int | None = None) -> Network:
     rng = np.random.Generator(np.random.PCG64(seed))

@@ -63,10 +63,10 @@ def qaoa48_shape(instance: int = 0):
     """(n, edges, outs) of the cut 48-qubit QAOA circuit ``instance``."""
     seed = 1000 * 4 + instance
     n, gates = circuits.qaoa_regular(48, seed)
-    for m in (5, 6):
+    for m, tries in ((5, 0), (6, 0), (5, 1), (6, 1), (7, 0)):
         try:
-            part = cutter.anneal_partition(n, gates, m, 16, seed=seed + 17 * m, free_qubits=range(24),
-                                           max_log2_elems=24)
+            part = cutter.anneal_partition(n, gates, m, 16, seed=seed + 17 * m + 7919 * tries,
+                                           free_qubits=range(24), max_log2_elems=24)
         except RuntimeError:
             continue
         cc = cutter.cut_circuit(n, gates, part)
@@ -81,6 +81,15 @@ def qaoa48(instance: int = 0, free_qubits=tuple(range(24))) -> Network:
     net = tensors.bin_restricted_network(n, edges, outs, free_qubits, seed=1000 * 4 + 500 + instance,
                                          meta={"workload": "qaoa48", "edges": edges,
                                                "circuit": "QAOA p=1, 3-regular graph, n=48"})
+    return net
+
+
+def qaoa48_timing(instance: int = 0, free_qubits=tuple(range(24))) -> Network:
+    """The restricted shapes of ``qaoa48(instance)`` with Gaussian values
+    (timing only: planner training and evaluation)."""
+    n, edges, outs = qaoa48_shape(instance)
+    net = tensors.restricted_shape_network(n, edges, outs, free_qubits, seed=1000 * 4 + 700 + instance)
+    net.meta.update({"workload": "qaoa48-timing", "instance": instance, "edges": edges})
     return net
 
 

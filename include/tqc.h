@@ -70,7 +70,9 @@ enum {
 enum {
     TQC_PLANNER_GREEDY = 0,      /* greedy pairwise merge on the predicted step time */
     TQC_PLANNER_EXHAUSTIVE = 1,  /* every contraction tree (m <= 9), best predicted time */
-    TQC_PLANNER_LEARNED = 2,     /* candidates ranked by the learned MLP cost model */
+    TQC_PLANNER_LEARNED = 2,     /* candidates within 10x of the best analytic estimate, ranked
+                                    by log(analytic seconds) + the learned MLP's output (a model
+                                    trained on log(measured / analytic seconds)) */
     TQC_PLANNER_AUTO = 3         /* exhaustive for m <= 8, else greedy */
 };
 
@@ -270,8 +272,10 @@ TQC_API int64_t tqc_noalloc_scratch_bytes(void);
  * Learned cost model (replaces the FLOP-count estimate of Eq.
  * classical_runtime, §V, which the paper finds consistently high).  A
  * multilayer perceptron, 3 hidden layers of 128 ReLU units, maps a plan's
- * TQC_PLAN_FEATURES features (tqc_plan_features) to the log of its measured
- * contraction time in seconds.  Forward, backward and Adam run in the
+ * TQC_PLAN_FEATURES features (tqc_plan_features) to a log-time target.  The
+ * learned planner (TQC_PLANNER_LEARNED) reads its output as the log of the
+ * plan's measured over its analytic contraction time, i.e. a correction to
+ * the planner's own estimate.  Forward, backward and Adam run in the
  * library's CUDA kernels on the current device (FP32); calls synchronise.
  *
  * Parameter layout (flat): W1 [F x 128], b1 [128], W2 [128 x 128], b2,

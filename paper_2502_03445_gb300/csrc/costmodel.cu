@@ -1,6 +1,7 @@
 // Learned cost model: a multilayer perceptron (3 hidden layers x 128 ReLU, one
-// linear output) that predicts the log of a plan's measured contraction time
-// from its features.  The paper divides a FLOP count by the GPU's FLOP rate
+// linear output) that predicts, from a plan's features, the log of its
+// measured over its analytic contraction time (the planner adds the analytic
+// log time back when it ranks candidates).  The paper divides a FLOP count by the GPU's FLOP rate
 // (Eq. classical_runtime, §V) and finds the estimate consistently high
 // (§VIII); this model is trained on timings the planner itself generates and
 // ranks candidate plans.  Forward, backward and Adam run in this file's own

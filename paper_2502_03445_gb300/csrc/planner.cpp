@@ -568,6 +568,8 @@ namespace {
 // Learned planner: plan every candidate tree completely (slicing, kernel
 // classes, layouts), predict each plan's log time with the cost model on the
 // GPU, keep the fastest.
+constexpr double kLearnedWindow = 10.0;  // analytic-estimate window of the ranked candidates
+
 tqc_status learned_tree(Net *net, const tqc_plan_opts &o, const NetBits &nb, int prec, const CostConsts &cc,
                         std::vector<std::array<uint64_t, 2>> *pairs, std::string *why) {
     if (!o.costmodel_path) {
@@ -584,17 +586,28 @@ tqc_status learned_tree(Net *net, const tqc_plan_opts &o, const NetBits &nb, int
         return TQC_ERR_INVALID;
     }
     auto cands = candidate_trees(nb, prec, cc, 24, 0x5EEDull + (uint64_t)nb.m);
-    std::vector<float> feats;
-    std::vector<int> ok;
+    // Build every candidate (slicing to the budget); the analytic model is the
+    // guard: only candidates within kLearnedWindow of its best estimate are
+    // ranked, so the network is never asked about shapes far outside the
+    // plans it was trained on.
+    std::vector<Plan> built(cands.size());
+    std::vector<char> valid(cands.size(), 0);
+    double best_pred = std::numeric_limits<double>::infinity();
     for (size_t i = 0; i < cands.size(); ++i) {
         std::vector<int32_t> ord = pairs_to_order(cands[i], nb.m);
         tqc_plan_opts oc = o;
         oc.order = ord.data();
         oc.n_order = nb.m - 1;
         oc.planner = TQC_PLANNER_GREEDY;
-        Plan cp;
-        if (build_plan(net, oc, &cp) != TQC_OK) continue;
-        for (double f : plan_features(cp)) feats.push_back((float)f);
+        if (build_plan(net, oc, &built[i]) != TQC_OK) continue;
+        valid[i] = 1;
+        best_pred = std::min(best_pred, built[i].predicted_s);
+    }
+    std::vector<float> feats;
+    std::vector<int> ok;
+    for (size_t i = 0; i < cands.size(); ++i) {
+        if (!valid[i] || built[i].predicted_s > kLearnedWindow * best_pred) continue;
+        for (double f : plan_features(built[i])) feats.push_back((float)f);
         ok.push_back((int)i);
     }
     if (ok.empty()) {
@@ -606,6 +619,8 @@ tqc_status learned_tree(Net *net, const tqc_plan_opts &o, const NetBits &nb, int
         *why = tqc_last_error();
         return TQC_ERR_CUDA;
     }
+    // the network predicts log(measured / analytic): add the analytic log time back
+    for (size_t k = 0; k < ok.size(); ++k) pred[k] += (float)std::log(built[(size_t)ok[k]].predicted_s);
     size_t best = std::min_element(pred.begin(), pred.end()) - pred.begin();
     *pairs = cands[ok[best]];
     return TQC_OK;

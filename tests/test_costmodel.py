@@ -151,8 +151,8 @@ def test_learned_model_beats_the_analytic_estimate(tmp_path):
     cm.save(path)
     err_mlp, err_flop, t_learned, t_analytic, t_best = [], [], [], [], []
     for net, recs in test_sets:
-        Xt, yt = costmodel.dataset(recs)
-        pred = cm.predict(Xt)
+        yt = np.log([r["seconds"] for r in recs])
+        pred = costmodel.predicted_log_seconds(cm, recs)
         ana = np.log([r["predicted_s"] for r in recs])
         err_mlp.append(np.mean(np.abs(pred - yt)))
         err_flop.append(np.mean(np.abs(ana - yt)))
