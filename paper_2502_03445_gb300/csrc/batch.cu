@@ -11,8 +11,9 @@
 // bounded (about one second); a wait that gives up raises an error word that
 // tqc_batch_status reports, and the remaining CTAs stop at their next item.
 //
-// The tensor-core tile here is synchronous per CTA (TMA load, tcgen05.mma,
-// commit, TMEM load, epilogue); two CTAs per SM overlap each other's phases.
+// One CTA per SM: tensor-core items (ranges of 16 tiles of one step) run
+// through a producer / MMA / direct-epilogue pipeline like the standalone
+// step kernel's; CUDA-core items are taken by four 4-warp groups.
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -32,16 +33,22 @@ struct tqc_plan {
 namespace tqc {
 namespace {
 
-constexpr int NT = 128;
+constexpr int BT = 576;                    // 18 warps: producer, MMA issuer, 16 epilogue / worker warps
+constexpr int EPIW = 16;
+constexpr int EPI = 32 * EPIW;
 constexpr long long BWAIT = 2000000000ll;  // ~1 s at the boost clock
 constexpr int64_t CHUNK = 1 << 16;          // ingest elements per item
+constexpr int RING = 196608;               // operand ring (tensor-core items) / worker buffers (CUDA-core items)
+constexpr int MAXST = 16;
+constexpr int BM = 128;
 
 enum ItemKind { IT_INGEST = 0, IT_STEP = 1, IT_STALL = 2 };
 
 struct alignas(128) BStep {
     CUtensorMap maps[4];  // A, B, A lo, B lo (tensor-core steps)
     StepArgs a;
-    int32_t klass, prec, bn, rowmajor, gmode, pitch;
+    int32_t klass, prec, bn, k_blocks, bres;
+    int32_t gmode;        // CUDA-core tiles: gather mode of the staged write-out
     int64_t col_tiles;
     int32_t dep[2];
     int64_t need[2];
@@ -56,19 +63,22 @@ struct BIngest {
 
 struct BItem {
     int32_t kind, idx;
-    int64_t tile;
+    int64_t tile, count;  // a range of tiles of one step
 };
 
-// shared memory carve-up (after 1024-byte alignment)
-constexpr int SM_STAGE = 65536;   // A, B, A lo, B lo: 4 x 16 KB (128-byte rows, <= 128 rows)
-constexpr int SM_STG = 128 * 68 * 4 > 64 * 132 * 4 ? 128 * 68 * 4 : 64 * 132 * 4;
-constexpr int SM_MISC = 256;
-constexpr int SMEM = 1024 + SM_STAGE + SM_STG + SM_MISC;
+// CUDA-core worker group: 4 warps, one 64 x 64 tile at a time
+constexpr int G_BK = 16, G_PA = 68, G_PB = 68, G_PS = 68;
+constexpr int G_STAGE = G_BK * (G_PA + G_PB) * 4;
+constexpr int G_BYTES = G_STAGE + 64 * G_PS * 4 + 128;
+static_assert(4 * G_BYTES <= RING, "worker buffers alias the ring");
+
+constexpr int SM_MISC = 2048;
+constexpr int SMEM = 1024 + RING + SM_MISC;
 
 __device__ __forceinline__ uint32_t s_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-__device__ __forceinline__ void bmbar_init(uint64_t *bar) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(s_u32(bar)) : "memory");
+__device__ __forceinline__ void bmbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(s_u32(bar)), "r"(count) : "memory");
 }
 __device__ __forceinline__ bool bmbar_try(uint64_t *bar, uint32_t parity) {
     uint32_t ok;
@@ -79,11 +89,35 @@ __device__ __forceinline__ bool bmbar_try(uint64_t *bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-__device__ __forceinline__ bool bmbar_wait(uint64_t *bar, uint32_t parity) {
+// Bounded wait for a phase; gives up (raising the CTA's abort flag) after
+// about a second or when another role already gave up.
+__device__ __forceinline__ bool bmbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag) {
     const long long t0 = clock64();
-    while (!bmbar_try(bar, parity))
-        if (clock64() - t0 > BWAIT) return false;
+    while (!bmbar_try(bar, parity)) {
+        if (*abort_flag) return false;
+        if (clock64() - t0 > BWAIT) {
+            *abort_flag = 1;
+            return false;
+        }
+    }
     return true;
+}
+__device__ __forceinline__ void bmbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(s_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void bmbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(s_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void btma_load(void *dst, const CUtensorMap *map, int c0, int c1, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            s_u32(dst)),
+        "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(s_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void bcommit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(s_u32(bar))
+                 : "memory");
 }
 
 __device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long *p) {
@@ -105,6 +139,7 @@ __device__ bool wait_counter(const unsigned long long *c, unsigned long long nee
 
 __device__ __forceinline__ void tc_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void bar_sync(int id, int n) { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory"); }
 
 __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
     uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
@@ -138,9 +173,9 @@ __device__ __forceinline__ void tmem_load32(uint32_t taddr, uint32_t (&r)[32]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-__device__ void ingest_range(const BIngest &it, int tid) {
+__device__ void ingest_range(const BIngest &it, int tid, int nt) {
     const IngestArgs &g = it.g;
-    for (int64_t d = it.lo + tid; d < it.hi; d += NT) {
+    for (int64_t d = it.lo + tid; d < it.hi; d += nt) {
         int64_t s = g.src_base;
         for (int b = 0; b < g.nbits; ++b)
             if (d >> b & 1) s += 1ll << g.srcpos[b];
@@ -164,229 +199,325 @@ __device__ void ingest_range(const BIngest &it, int tid) {
     }
 }
 
-// 64 x 64 CUDA-core tile: 128 threads, 4 x 8 results each.
-__device__ void simt_tile(const BStep &st, const EpiTables *tb, int64_t tile, uint8_t *stage, float *stg,
-                          uint64_t *base_slot, int tid) {
-    constexpr int BM = 64, BN = 64, TM = 4, TN = 8, BK = 16, PA = BM + 4, PB = BN + 4, PS = BN + 4;
+// 64 x 64 CUDA-core tile computed by one 4-warp group (named barrier `bid`,
+// 128 threads; gt = thread index in the group): 4 x 8 results per thread,
+// staged row-major and written in destination order.
+__device__ void simt_tile(const BStep &st, const EpiTables *tb, int64_t tile, uint8_t *buf, int bid, int gt) {
+    constexpr int GBM = 64, GBN = 64, TM = 4, TN = 8;
     const StepArgs &a = st.a;
     const EpiParams &e = a.epi;
-    float *As = (float *)stage, *Bs = As + BK * PA;
+    float *As = (float *)buf, *Bs = As + G_BK * G_PA, *stg = (float *)(buf + G_STAGE);
+    uint64_t *base_slot = (uint64_t *)(buf + G_STAGE + 64 * G_PS * 4);
     const int Me = 1 << e.a_bits, Ne = 1 << e.b_bits;
     const int64_t K = 1ll << a.kb;
     const int lkc = a.kb < 4 ? a.kb : 4, kc = 1 << lkc;
     const float *A = (const float *)a.A, *B = (const float *)a.B;
-    const int tx = tid % (BN / TN), ty = tid / (BN / TN);
+    const int tx = gt % (GBN / TN), ty = gt / (GBN / TN);
     const int64_t rt = tile / st.col_tiles, ct = tile - rt * st.col_tiles;
     const int64_t r0 = rt << e.a_bits, c0 = ct << e.b_bits;
-    if (tid == 0) *base_slot = tile_base(e, (uint64_t)rt, (uint64_t)ct);
+    if (gt == 0) *base_slot = tile_base(e, (uint64_t)rt, (uint64_t)ct);
     float acc[TM][TN];
 #pragma unroll
     for (int u = 0; u < TM; ++u)
 #pragma unroll
         for (int v = 0; v < TN; ++v) acc[u][v] = 0.f;
     for (int64_t k0 = 0; k0 < K; k0 += kc) {
-        for (int idx = tid; idx < (BM << lkc); idx += NT) {
+        for (int idx = gt; idx < (GBM << lkc); idx += 128) {
             int i = idx >> lkc, kk = idx & (kc - 1);
-            As[kk * PA + i] = i < Me ? A[(r0 + i) * K + k0 + kk] : 0.f;
+            As[kk * G_PA + i] = i < Me ? A[(r0 + i) * K + k0 + kk] : 0.f;
         }
-        for (int idx = tid; idx < (BN << lkc); idx += NT) {
+        for (int idx = gt; idx < (GBN << lkc); idx += 128) {
             int j = idx >> lkc, kk = idx & (kc - 1);
-            Bs[kk * PB + j] = j < Ne ? B[(c0 + j) * K + k0 + kk] : 0.f;
+            Bs[kk * G_PB + j] = j < Ne ? B[(c0 + j) * K + k0 + kk] : 0.f;
         }
-        __syncthreads();
+        bar_sync(bid, 128);
         for (int kk = 0; kk < kc; ++kk) {
             float af[TM], bf[TN];
 #pragma unroll
-            for (int u = 0; u < TM; ++u) af[u] = As[kk * PA + ty * TM + u];
+            for (int u = 0; u < TM; ++u) af[u] = As[kk * G_PA + ty * TM + u];
 #pragma unroll
-            for (int v = 0; v < TN; v += 4) *(float4 *)&bf[v] = *(const float4 *)&Bs[kk * PB + tx * TN + v];
+            for (int v = 0; v < TN; v += 4) *(float4 *)&bf[v] = *(const float4 *)&Bs[kk * G_PB + tx * TN + v];
 #pragma unroll
             for (int u = 0; u < TM; ++u)
 #pragma unroll
                 for (int v = 0; v < TN; ++v) acc[u][v] = fmaf(af[u], bf[v], acc[u][v]);
         }
-        __syncthreads();
+        bar_sync(bid, 128);
     }
 #pragma unroll
     for (int u = 0; u < TM; ++u)
 #pragma unroll
         for (int v = 0; v < TN; v += 4)
-            *(float4 *)&stg[(ty * TM + u) * PS + tx * TN + v] =
+            *(float4 *)&stg[(ty * TM + u) * G_PS + tx * TN + v] =
                 make_float4(acc[u][v], acc[u][v + 1], acc[u][v + 2], acc[u][v + 3]);
-    __syncthreads();
-    epi_readout(tb, stg, e, *base_slot, Me * Ne, tid, NT, st.gmode);
+    bar_sync(bid, 128);
+    epi_readout(tb, stg, e, *base_slot, Me * Ne, gt, 128, st.gmode);
+    bar_sync(bid, 128);
 }
 
-// 128 x bn tensor-core tile (synchronous: TMA, MMA, TMEM load, epilogue).
-__device__ bool umma_tile(const BStep &st, const EpiTables *tb, int64_t tile, uint8_t *stage, float *stg,
-                          uint64_t *bars, uint64_t *base_slot, uint32_t tmem, uint32_t &tph, uint32_t &mph,
-                          int *ok_slot, int tid) {
-    const StepArgs &a = st.a;
-    const EpiParams &e = a.epi;
-    const int warp = tid >> 5, lane = tid & 31;
-    const int64_t rt = tile / st.col_tiles, ct = tile - rt * st.col_tiles;
-    const int elem = st.prec == TQC_PREC_TF32 ? 4 : 2;
-    const int bk = 128 / elem;
-    const int kblocks = (int)((1ll << a.kb) / bk);
-    const bool x3 = st.prec == TQC_PREC_BF16X3;
-    const uint32_t idesc = (1u << 4) | ((st.prec == TQC_PREC_TF32 ? 2u : 1u) << 7) |
-                           ((st.prec == TQC_PREC_TF32 ? 2u : 1u) << 10) | ((uint32_t)(st.bn >> 3) << 17) |
-                           ((uint32_t)(128 >> 4) << 24);
-    if (tid == 0) {
-        bool ok = true;
-        asm volatile("fence.proxy.async.global;" ::: "memory");
-        const uint32_t bytes = (uint32_t)((128 + st.bn) * 128 * (x3 ? 2 : 1));
-        uint8_t *sA = stage, *sB = stage + 16384, *sAl = stage + 32768, *sBl = stage + 49152;
-        for (int kb = 0; kb < kblocks && ok; ++kb) {
-            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(s_u32(&bars[0])), "r"(bytes)
-                         : "memory");
-            const CUtensorMap *mp = st.maps;
-            const int c0 = kb * bk;
-            const int ra = (int)(rt * 128), rb = (int)(ct * st.bn);
-#define BT_LOAD(dst, map, y)                                                                                       \
-    asm volatile(                                                                                                  \
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"( \
-            s_u32(dst)),                                                                                           \
-        "l"((uint64_t)(map)), "r"(c0), "r"(y), "r"(s_u32(&bars[0]))                                                \
-        : "memory")
-            BT_LOAD(sA, &mp[0], ra);
-            BT_LOAD(sB, &mp[1], rb);
-            if (x3) {
-                BT_LOAD(sAl, &mp[2], ra);
-                BT_LOAD(sBl, &mp[3], rb);
-            }
-#undef BT_LOAD
-            ok = bmbar_wait(&bars[0], tph);
-            tph ^= 1u;
-            if (!ok) break;
-            tc_after();
-            const uint32_t a0 = s_u32(sA), b0 = s_u32(sB), al = s_u32(sAl), bl = s_u32(sBl);
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const uint64_t da = sw128_desc(a0 + 32 * k), db = sw128_desc(b0 + 32 * k);
-                mma_issue(st.prec, tmem, da, db, idesc, (kb | k) != 0);
-                if (x3) {
-                    mma_issue(st.prec, tmem, da, sw128_desc(bl + 32 * k), idesc, 1u);
-                    mma_issue(st.prec, tmem, sw128_desc(al + 32 * k), db, idesc, 1u);
-                }
-            }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                             s_u32(&bars[1]))
-                         : "memory");
-            ok = bmbar_wait(&bars[1], mph);  // the stage is reused by the next k-block
-            mph ^= 1u;
-        }
-        *ok_slot = ok ? 1 : 0;
-    }
-    tc_before();
-    __syncthreads();
-    tc_after();
-    if (!*ok_slot) return false;
-    const int subs = st.bn / 64;
-    const int Me = 1 << e.a_bits, Ne = 1 << e.b_bits;
-    const int row = warp * 32 + lane;
-    for (int h = 0; h < subs; ++h) {
-        if (tid == 0) *base_slot = tile_base(e, (uint64_t)rt, (uint64_t)(ct * subs + h));
-        for (int c = 0; c < 2; ++c) {
-            uint32_t r[32];
-            tmem_load32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(h * 64 + c * 32), r);
-            if (row < Me) {
-                if (st.rowmajor) {
-#pragma unroll
-                    for (int j = 0; j < 32; j += 4)
-                        if (c * 32 + j < Ne)
-                            *(float4 *)(stg + row * st.pitch + c * 32 + j) =
-                                make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]), __uint_as_float(r[j + 2]),
-                                            __uint_as_float(r[j + 3]));
-                } else {
-#pragma unroll
-                    for (int j = 0; j < 32; ++j)
-                        if (c * 32 + j < Ne) stg[(c * 32 + j) * st.pitch + row] = __uint_as_float(r[j]);
-                }
-            }
-        }
-        __syncthreads();
-        epi_readout(tb, stg, e, *base_slot, Me * Ne, tid, NT, st.gmode);
-        __syncthreads();
-    }
-    tc_before();
-    return true;
-}
+// Shared control block of the CTA (after the ring).
+struct Ctl {
+    uint64_t full[MAXST], empty[MAXST];
+    uint64_t tfull[2], tempty[2], bfull, drain;
+    uint32_t tmem;
+    int abort_flag;
+    int64_t item;
+    int ok;
+};
 
-__global__ void __launch_bounds__(NT, 2)
+// One CTA per SM drains the work list.  A tensor-core item is a range of
+// tiles of one step, run through the same pipeline as the standalone kernel:
+// warp 0 loads k-blocks with TMA into a ring of stages, warp 1 issues
+// tcgen05.mma into one of two TMEM accumulators, and the 16 other warps load
+// each accumulator and store it straight to the result layout.  Every stage
+// keeps its own phase bits, so items of different stage sizes restart the
+// ring at stage 0.  A CUDA-core item is a range of 64 x 64 tiles taken by four
+// 4-warp groups; an ingest item a range of leaf elements.  Between items the
+// whole CTA synchronises: the ring and the group buffers share memory.
+__global__ void __launch_bounds__(BT, 1)
     batch_kernel(const BItem *items, int64_t n_items, const BStep *steps, const EpiTables *tables, const BIngest *ing,
                  unsigned long long *counters, unsigned long long *next, int *err) {
     extern __shared__ uint8_t raw[];
     uint8_t *sm = (uint8_t *)(((uintptr_t)raw + 1023) & ~(uintptr_t)1023);
-    uint8_t *stage = sm;
-    float *stg = (float *)(sm + SM_STAGE);
-    uint64_t *bars = (uint64_t *)(sm + SM_STAGE + SM_STG);  // [0] TMA, [1] MMA
-    uint32_t *tmem_slot = (uint32_t *)(bars + 2);
-    int64_t *item_slot = (int64_t *)(bars + 3);
-    uint64_t *base_slot = (uint64_t *)(bars + 4);
-    int *ok_slot = (int *)(bars + 5);
-    const int tid = threadIdx.x, warp = tid >> 5;
+    uint8_t *ring = sm;
+    Ctl *ctl = (Ctl *)(sm + RING);
+    volatile int *abort_flag = &ctl->abort_flag;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (tid == 0) {
-        bmbar_init(&bars[0]);
-        bmbar_init(&bars[1]);
+        for (int s = 0; s < MAXST; ++s) {
+            bmbar_init(&ctl->full[s], 1);
+            bmbar_init(&ctl->empty[s], 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            bmbar_init(&ctl->tfull[a], 1);
+            bmbar_init(&ctl->tempty[a], EPIW);
+        }
+        bmbar_init(&ctl->bfull, 1);
+        bmbar_init(&ctl->drain, 1);
+        ctl->abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;" ::"r"(s_u32(tmem_slot))
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(s_u32(&ctl->tmem))
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     tc_before();
     __syncthreads();
     tc_after();
-    const uint32_t tmem = *tmem_slot;
-    uint32_t tph = 0, mph = 0;
+    const uint32_t tmem = ctl->tmem;
+    // role state that persists across items
+    uint32_t used = 0, eph = 0, fph = 0;  // producer: stage used / empty phase bits; MMA: full phase bits
+    uint32_t bph = 0;                     // resident-B phase (producer and MMA)
+    int64_t lt = 0;                       // accumulator sequence (MMA and epilogue)
+    bool issued = false;                  // MMA: anything to drain at exit
     for (;;) {
-        if (tid == 0) *item_slot = *(volatile int *)err ? n_items : (int64_t)atomicAdd(next, 1ull);
+        if (tid == 0) {
+            const int64_t it = (*(volatile int *)err || *abort_flag) ? n_items : (int64_t)atomicAdd(next, 1ull);
+            int ok = 1;
+            if (it < n_items) {
+                const BItem item = items[it];
+                if (item.kind == IT_STALL) {
+                    ok = wait_counter(&counters[item.idx], 1ull, err) ? 1 : 0;  // nothing increments it
+                } else if (item.kind == IT_STEP) {
+                    const BStep &st = steps[item.idx];
+                    for (int d = 0; d < 2 && ok; ++d)
+                        if (st.dep[d] >= 0 && !wait_counter(&counters[st.dep[d]], (unsigned long long)st.need[d], err))
+                            ok = 0;
+                    if (ok && st.klass == KC_UMMA) asm volatile("fence.proxy.async.global;" ::: "memory");
+                }
+                if (!ok) atomicExch(err, 1);
+            }
+            ctl->item = it;
+            ctl->ok = ok;
+        }
         __syncthreads();
-        const int64_t it = *item_slot;
-        __syncthreads();
+        const int64_t it = ctl->item;
         if (it >= n_items) break;
         const BItem item = items[it];
-        if (item.kind == IT_INGEST) {
-            const BIngest &g = ing[item.idx];
-            ingest_range(g, tid);
-            __threadfence();
-            __syncthreads();
-            if (tid == 0) atomicAdd(&counters[g.done], 1ull);
-            continue;
-        }
-        if (tid == 0) {
-            bool ok = true;
-            if (item.kind == IT_STALL) {
-                ok = wait_counter(&counters[item.idx], 1ull, err);  // nothing increments it
-            } else {
-                const BStep &st = steps[item.idx];
-                for (int d = 0; d < 2 && ok; ++d)
-                    if (st.dep[d] >= 0) ok = wait_counter(&counters[st.dep[d]], (unsigned long long)st.need[d], err);
+        const bool run = ctl->ok && item.kind != IT_STALL;
+        if (run && item.kind == IT_INGEST) {
+            if (warp >= 2) ingest_range(ing[item.idx], tid - 64, EPI);
+        } else if (run && steps[item.idx].klass != KC_UMMA) {
+            if (warp >= 2) {
+                const int g = (warp - 2) >> 2;
+                for (int64_t t = item.tile + g; t < item.tile + item.count; t += 4)
+                    simt_tile(steps[item.idx], &tables[item.idx], t, ring + g * G_BYTES, 2 + g, (tid - 64) & 127);
             }
-            if (!ok) atomicExch(err, 1);
-            *ok_slot = ok ? 1 : 0;
+        } else if (run) {
+            const BStep &st = steps[item.idx];
+            const bool x3 = st.prec == TQC_PREC_BF16X3;
+            const int planes = x3 ? 2 : 1;
+            const int a_bytes = BM * 128, b_bytes = st.bn * 128;
+            const int sbytes = st.bres ? planes * a_bytes : planes * (a_bytes + b_bytes);
+            const int nfit = (RING - (st.bres ? planes * b_bytes : 0)) / sbytes;
+            const int nst = nfit < MAXST ? nfit : MAXST;
+            uint8_t *bsm = ring + RING - planes * b_bytes;
+            const int bk = st.prec == TQC_PREC_TF32 ? 32 : 64;
+            const int64_t t_end = item.tile + item.count;
+            if (warp == 0) {
+                // ---------------------------------------- TMA producer
+                if (lane == 0) {
+                    if (st.bres) {
+                        bmbar_expect_tx(&ctl->bfull, (uint32_t)(planes * b_bytes));
+                        btma_load(bsm, &st.maps[1], 0, 0, &ctl->bfull);
+                        if (x3) btma_load(bsm + b_bytes, &st.maps[3], 0, 0, &ctl->bfull);
+                    }
+                    int s = 0;
+                    for (int64_t tile = item.tile; tile < t_end && !*abort_flag; ++tile) {
+                        const int rt = (int)(tile / st.col_tiles), ct = (int)(tile - (int64_t)rt * st.col_tiles);
+                        for (int kb = 0; kb < st.k_blocks; ++kb) {
+                            if (used >> s & 1) {
+                                if (!bmbar_wait(&ctl->empty[s], eph >> s & 1, abort_flag)) break;
+                                eph ^= 1u << s;
+                            }
+                            used |= 1u << s;
+                            uint8_t *sa = ring + s * sbytes;
+                            bmbar_expect_tx(&ctl->full[s], (uint32_t)sbytes);
+                            btma_load(sa, &st.maps[0], kb * bk, rt * BM, &ctl->full[s]);
+                            if (st.bres) {
+                                if (x3) btma_load(sa + a_bytes, &st.maps[2], kb * bk, rt * BM, &ctl->full[s]);
+                            } else {
+                                btma_load(sa + a_bytes, &st.maps[1], kb * bk, ct * st.bn, &ctl->full[s]);
+                                if (x3) {
+                                    btma_load(sa + a_bytes + b_bytes, &st.maps[2], kb * bk, rt * BM, &ctl->full[s]);
+                                    btma_load(sa + 2 * a_bytes + b_bytes, &st.maps[3], kb * bk, ct * st.bn, &ctl->full[s]);
+                                }
+                            }
+                            s = s + 1 == nst ? 0 : s + 1;
+                        }
+                    }
+                }
+            } else if (warp == 1) {
+                // ---------------------------------------- MMA issuer
+                if (lane == 0) {
+                    const uint32_t idesc = (1u << 4) | ((st.prec == TQC_PREC_TF32 ? 2u : 1u) << 7) |
+                                           ((st.prec == TQC_PREC_TF32 ? 2u : 1u) << 10) |
+                                           ((uint32_t)(st.bn >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+                    bool ok = true;
+                    if (st.bres) {
+                        ok = bmbar_wait(&ctl->bfull, bph, abort_flag);
+                        tc_after();
+                    }
+                    int s = 0;
+                    for (int64_t tile = item.tile; ok && tile < t_end; ++tile, ++lt) {
+                        const int acc = (int)(lt & 1);
+                        if (!bmbar_wait(&ctl->tempty[acc], (uint32_t)(((lt >> 1) & 1) ^ 1), abort_flag)) break;
+                        tc_after();
+                        const uint32_t d = tmem + (uint32_t)(acc * 256);
+                        for (int kb = 0; kb < st.k_blocks; ++kb) {
+                            if (!bmbar_wait(&ctl->full[s], fph >> s & 1, abort_flag)) {
+                                ok = false;
+                                break;
+                            }
+                            fph ^= 1u << s;
+                            tc_after();
+                            const uint32_t a0 = s_u32(ring + s * sbytes);
+                            const uint32_t b0 = st.bres ? s_u32(bsm) : a0 + (uint32_t)a_bytes;
+                            const uint32_t al = st.bres ? a0 + (uint32_t)a_bytes : b0 + (uint32_t)b_bytes;
+                            const uint32_t bl = st.bres ? b0 + (uint32_t)b_bytes : al + (uint32_t)a_bytes;
+#pragma unroll
+                            for (int k = 0; k < 4; ++k) {
+                                const uint64_t da = sw128_desc(a0 + 32 * k), db = sw128_desc(b0 + 32 * k);
+                                mma_issue(st.prec, d, da, db, idesc, (kb | k) != 0);
+                                if (x3) {
+                                    mma_issue(st.prec, d, da, sw128_desc(bl + 32 * k), idesc, 1u);
+                                    mma_issue(st.prec, d, sw128_desc(al + 32 * k), db, idesc, 1u);
+                                }
+                            }
+                            bcommit(&ctl->empty[s]);
+                            issued = true;
+                            s = s + 1 == nst ? 0 : s + 1;
+                        }
+                        if (!ok) break;
+                        bcommit(&ctl->tfull[acc]);
+                    }
+                    if (st.bres) bph ^= 1u;
+                }
+            } else {
+                // ---------------------------------------- direct epilogue
+                const EpiParams &e = st.a.epi;
+                const int q = (warp - 2) >> 2, lane_grp = warp & 3;
+                const int row = lane_grp * 32 + lane;
+                const int Me = 1 << e.a_bits, Ne = 1 << e.b_bits;
+                const int subs = st.bn / 64;
+                const uint64_t grow = pdep64((uint64_t)pdep32((uint32_t)row, e.lowRc), e.tileMask);
+                const uint64_t colmask = pdep64((uint64_t)e.lowCc, e.tileMask);
+                const bool full = Me == BM && Ne == 64;
+                const int vw = !full ? 1 : (((e.lowCc & 3u) == 3u && e.L >= 2) ? 4 : ((e.lowCc & 1u) && e.L >= 1 ? 2 : 1));
+                const uint64_t mstep = vw == 4 ? colmask & (colmask - 1) & ((colmask & (colmask - 1)) - 1)
+                                               : (vw == 2 ? colmask & (colmask - 1) : colmask);
+                const double sd = (e.mode == EPI_OUT_F32 || e.mode == EPI_OUT_F64) ? e.zinfo[1] : 1.0;
+                const float sf = (float)sd;
+                int64_t my_lt = lt;
+                for (int64_t tile = item.tile; tile < t_end; ++tile, ++my_lt) {
+                    const int acc = (int)(my_lt & 1);
+                    if (lane == 0) bmbar_wait(&ctl->tfull[acc], (uint32_t)((my_lt >> 1) & 1), abort_flag);
+                    __syncwarp();
+                    if (*abort_flag) break;
+                    tc_after();
+                    const uint64_t rt = (uint64_t)(tile / st.col_tiles);
+                    const uint64_t ct = (uint64_t)(tile - (int64_t)rt * st.col_tiles);
+                    const uint64_t base = warp_pdep64(rt, e.highR) | warp_pdep64(ct * (uint64_t)subs, e.highC);
+                    // this warp's 32-column chunks: q, q + 4, ... below BN (none for
+                    // q >= 2 when BN = 64); every warp frees the accumulator once
+                    const int nch = q * 32 < st.bn ? (st.bn - q * 32 + 127) / 128 : 0;
+                    if (nch == 0) {
+                        tc_before();
+                        __syncwarp();
+                        if (lane == 0) bmbar_arrive(&ctl->tempty[acc]);
+                    }
+                    for (int c = 0; c < nch; ++c) {
+                        const int col0 = q * 32 + 128 * c;
+                        uint32_t r[32];
+                        tmem_load32(tmem + ((uint32_t)(lane_grp * 32) << 16) + (uint32_t)(acc * 256 + col0), r);
+                        if (c == nch - 1) {
+                            tc_before();
+                            __syncwarp();
+                            if (lane == 0) bmbar_arrive(&ctl->tempty[acc]);
+                        }
+                        const int j0 = col0 % 64;
+                        const uint64_t o = base + grow + pdep64((uint64_t)j0, colmask) +
+                                           pdep64((uint64_t)(col0 / 64), e.highC);
+                        if (full) {
+                            direct_run32_any(e, vw, o, mstep, r, sf, sd);
+                        } else if (row < Me && j0 < Ne) {
+                            uint64_t x = 0;
+                            const int nc = Ne - j0 < 32 ? Ne - j0 : 32;
+                            for (int j = 0; j < nc; ++j) {
+                                const float v = __uint_as_float(r[j]);
+                                store_run_f32(e, o + x, &v, 1, sd);
+                                x = ((x | ~colmask) + 1) & colmask;
+                            }
+                        }
+                    }
+                }
+            }
+            // the accumulator sequence advances by the item's tiles in every role
+            if (warp != 1) lt += item.count;
         }
-        __syncthreads();
-        if (!*ok_slot || item.kind == IT_STALL) continue;
-        const BStep &st = steps[item.idx];
-        bool ok = true;
-        if (st.klass == KC_UMMA)
-            ok = umma_tile(st, &tables[item.idx], item.tile, stage, stg, bars, base_slot, tmem, tph, mph, ok_slot, tid);
-        else
-            simt_tile(st, &tables[item.idx], item.tile, stage, stg, base_slot, tid);
+        // the ring and the group buffers share memory: order generic writes
+        // before the next item's TMA writes, and finish every role first
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __threadfence();
         __syncthreads();
         if (tid == 0) {
-            if (ok) atomicAdd(&counters[st.done], 1ull);
-            else atomicExch(err, 1);
+            if (*abort_flag) atomicExch(err, 1);
+            else if (run) atomicAdd(&counters[item.kind == IT_INGEST ? ing[item.idx].done : steps[item.idx].done], 1ull);
         }
     }
+    if (warp == 1 && lane == 0 && issued) {
+        // every MMA issued so far has completed once this commit arrives
+        bcommit(&ctl->drain);
+        const long long t0 = clock64();
+        while (!bmbar_try(&ctl->drain, 0) && clock64() - t0 < BWAIT) {
+        }
+    }
+    tc_before();
     __syncthreads();
-    if (warp == 0) {
+    if (warp == 1) {
         tc_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(tmem) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
     }
 }
 
@@ -499,7 +630,7 @@ tqc_status build_batch(Plan *const *plans, void *const *outs, int n, Batch *b) {
             for (int64_t lo = 0; lo < total; lo += CHUNK) {
                 bi.lo = lo;
                 bi.hi = std::min(total, lo + CHUNK);
-                leveled.push_back({0, BItem{IT_INGEST, (int)ing.size(), 0}});
+                leveled.push_back({0, BItem{IT_INGEST, (int)ing.size(), 0, 1}});
                 ing.push_back(bi);
                 ++n_chunks;
             }
@@ -529,24 +660,25 @@ tqc_status build_batch(Plan *const *plans, void *const *outs, int n, Batch *b) {
                 bs.a.epi.mode = exec_epi_mode(tc.storage);
             }
             int64_t row_tiles = (int64_t)1 << (sp.mb - bs.a.epi.a_bits);
+            int64_t per_item;
             if (sp.klass == KC_UMMA) {
-                bs.bn = sp.nb >= 7 ? 128 : 64;
-                const int lbn = bs.bn == 128 ? 7 : 6;
+                bs.bn = sp.nb >= 8 ? 256 : (sp.nb >= 7 ? 128 : 64);
+                const int lbn = bs.bn == 256 ? 8 : (bs.bn == 128 ? 7 : 6);
                 bs.col_tiles = sp.nb >= lbn ? (int64_t)1 << (sp.nb - lbn) : 1;
-                StagePick pk = pick_staging(bs.a.epi.lowRc, bs.a.epi.lowCc);
-                bs.rowmajor = pk.rowmajor;
-                bs.gmode = pk.gmode;
-                bs.pitch = pk.rowmajor ? 68 : 132;
+                bs.k_blocks = (int)(((int64_t)1 << sp.kb) / (sp.prec == TQC_PREC_TF32 ? 32 : 64));
+                if (bs.k_blocks < 1) return fail(TQC_ERR_UNSUPPORTED, "batch: tensor-core step with K below one k-block");
+                bs.bres = bs.k_blocks == 1 && bs.col_tiles == 1;
                 if (umma_make_maps(sp.prec, bs.a, bs.bn, bs.maps) != cudaSuccess)
                     return fail(TQC_ERR_CUDA, "batch: tensor map of plan " + std::to_string(pi));
+                per_item = 16;
             } else {
                 bs.bn = 64;
                 bs.col_tiles = (int64_t)1 << (sp.nb - bs.a.epi.b_bits);
-                bs.rowmajor = 1;
                 bs.gmode = gather_mode(bs.a.epi.lowCc);
-                bs.pitch = 68;
+                per_item = 16;
             }
             const int64_t n_tiles = row_tiles * bs.col_tiles;
+            const int64_t n_step_items = (n_tiles + per_item - 1) / per_item;
             bs.dep[0] = counter_of[sp.a];
             bs.need[0] = tiles_of[sp.a];
             bs.dep[1] = counter_of[sp.b];
@@ -554,18 +686,19 @@ tqc_status build_batch(Plan *const *plans, void *const *outs, int n, Batch *b) {
             if (bs.dep[1] == bs.dep[0]) bs.dep[1] = -1;
             bs.done = n_counters++;
             counter_of[sp.c] = bs.done;
-            tiles_of[sp.c] = n_tiles;
+            tiles_of[sp.c] = n_step_items;  // the counter counts finished items
             const int lvl = 1 + std::max(level_of[sp.a], level_of[sp.b]);
             level_of[sp.c] = lvl;
             EpiTables tb;
-            host_tables(&tb, bs.a.epi, bs.rowmajor != 0, bs.pitch);
+            host_tables(&tb, bs.a.epi, true, 68);  // staged write-out of the 64 x 64 CUDA-core tiles
             const int si = (int)steps.size();
             steps.push_back(bs);
             tables.push_back(tb);
-            for (int64_t t = 0; t < n_tiles; ++t) leveled.push_back({lvl, BItem{IT_STEP, si, t}});
+            for (int64_t t = 0; t < n_tiles; t += per_item)
+                leveled.push_back({lvl, BItem{IT_STEP, si, t, std::min(per_item, n_tiles - t)}});
         }
     }
-    if (g_inject_stall) leveled.insert(leveled.begin(), {0, BItem{IT_STALL, n_counters++, 0}});
+    if (g_inject_stall) leveled.insert(leveled.begin(), {0, BItem{IT_STALL, n_counters++, 0, 0}});
     std::stable_sort(leveled.begin(), leveled.end(), [](auto &x, auto &y) { return x.first < y.first; });
     for (auto &li : leveled) items.push_back(li.second);
     b->n_items = (int64_t)items.size();
@@ -621,8 +754,8 @@ tqc_status tqc_contract_batch(const tqc_plan_t *plans, void *const *d_outs, int3
     cudaError_t e = cudaMemsetAsync(g_batch.d_counters, 0, sizeof(unsigned long long) * (g_batch.n_counters + 1), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(g_batch.d_err, 0, sizeof(int), s);
     if (e != cudaSuccess) return fail(TQC_ERR_CUDA, std::string("batch reset: ") + cudaGetErrorString(e));
-    const int grid = 2 * sm_count();
-    batch_kernel<<<grid, NT, SMEM, s>>>(g_batch.d_items, g_batch.n_items, g_batch.d_steps, g_batch.d_tables,
+    const int grid = sm_count();
+    batch_kernel<<<grid, BT, SMEM, s>>>(g_batch.d_items, g_batch.n_items, g_batch.d_steps, g_batch.d_tables,
                                         g_batch.d_ing, g_batch.d_counters, g_batch.d_counters + g_batch.n_counters,
                                         g_batch.d_err);
     e = cudaGetLastError();
