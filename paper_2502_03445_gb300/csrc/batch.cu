@@ -69,7 +69,8 @@ struct BItem {
 // CUDA-core worker group: 4 warps, one 64 x 64 tile at a time
 constexpr int G_BK = 16, G_PA = 68, G_PB = 68, G_PS = 68;
 constexpr int G_STAGE = G_BK * (G_PA + G_PB) * 4;
-constexpr int G_BYTES = G_STAGE + 64 * G_PS * 4 + 128;
+constexpr int G_TABLES = 2 * G_STAGE + 64 * G_PS * 4;  // the step's write-out tables, copied per item
+constexpr int G_BYTES = G_TABLES + (int)sizeof(EpiTables);
 static_assert(4 * G_BYTES <= RING, "worker buffers alias the ring");
 
 constexpr int SM_MISC = 2048;
@@ -199,60 +200,101 @@ __device__ void ingest_range(const BIngest &it, int tid, int nt) {
     }
 }
 
-// 64 x 64 CUDA-core tile computed by one 4-warp group (named barrier `bid`,
-// 128 threads; gt = thread index in the group): 4 x 8 results per thread,
-// staged row-major and written in destination order.
-__device__ void simt_tile(const BStep &st, const EpiTables *tb, int64_t tile, uint8_t *buf, int bid, int gt) {
-    constexpr int GBM = 64, GBN = 64, TM = 4, TN = 8;
+__device__ __forceinline__ void cp_async4(float *dst, const float *src, bool valid) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(s_u32(dst)), "l"(src), "r"(valid ? 4 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// Issue the copies of one K chunk of a 64 x 64 tile's operands into a stage
+// (A transposed to [k][row], B to [k][col]; rows / columns past the step's
+// extent read as zeros).
+__device__ __forceinline__ void simt_load(const BStep &st, int64_t tile, int64_t k0, float *stage, int gt) {
     const StepArgs &a = st.a;
     const EpiParams &e = a.epi;
-    float *As = (float *)buf, *Bs = As + G_BK * G_PA, *stg = (float *)(buf + G_STAGE);
-    uint64_t *base_slot = (uint64_t *)(buf + G_STAGE + 64 * G_PS * 4);
     const int Me = 1 << e.a_bits, Ne = 1 << e.b_bits;
     const int64_t K = 1ll << a.kb;
     const int lkc = a.kb < 4 ? a.kb : 4, kc = 1 << lkc;
     const float *A = (const float *)a.A, *B = (const float *)a.B;
-    const int tx = gt % (GBN / TN), ty = gt / (GBN / TN);
     const int64_t rt = tile / st.col_tiles, ct = tile - rt * st.col_tiles;
     const int64_t r0 = rt << e.a_bits, c0 = ct << e.b_bits;
-    if (gt == 0) *base_slot = tile_base(e, (uint64_t)rt, (uint64_t)ct);
-    float acc[TM][TN];
-#pragma unroll
-    for (int u = 0; u < TM; ++u)
-#pragma unroll
-        for (int v = 0; v < TN; ++v) acc[u][v] = 0.f;
-    for (int64_t k0 = 0; k0 < K; k0 += kc) {
-        for (int idx = gt; idx < (GBM << lkc); idx += 128) {
-            int i = idx >> lkc, kk = idx & (kc - 1);
-            As[kk * G_PA + i] = i < Me ? A[(r0 + i) * K + k0 + kk] : 0.f;
-        }
-        for (int idx = gt; idx < (GBN << lkc); idx += 128) {
-            int j = idx >> lkc, kk = idx & (kc - 1);
-            Bs[kk * G_PB + j] = j < Ne ? B[(c0 + j) * K + k0 + kk] : 0.f;
-        }
+    float *As = stage, *Bs = stage + G_BK * G_PA;
+    for (int idx = gt; idx < (64 << lkc); idx += 128) {
+        const int i = idx >> lkc, kk = idx & (kc - 1);
+        cp_async4(&As[kk * G_PA + i], A + (i < Me ? (r0 + i) * K + k0 + kk : 0), i < Me);
+    }
+    for (int idx = gt; idx < (64 << lkc); idx += 128) {
+        const int j = idx >> lkc, kk = idx & (kc - 1);
+        cp_async4(&Bs[kk * G_PB + j], B + (j < Ne ? (c0 + j) * K + k0 + kk : 0), j < Ne);
+    }
+}
+
+// The tiles t0, t0 + 4, ... < t_end of one CUDA-core step, computed by one
+// 4-warp group (named barrier `bid`, 128 threads, gt = thread index in the
+// group): 64 x 64 tiles, 4 x 8 results per thread, staged row-major and
+// written in destination order.  The first K chunk of the next tile is
+// copied (cp.async) into the other stage while the current tile computes and
+// writes out.
+__device__ void simt_range(const BStep &st, const EpiTables *tb, int64_t t0, int64_t t_end, uint8_t *buf, int bid,
+                           int gt) {
+    constexpr int TM = 4, TN = 8;
+    const StepArgs &a = st.a;
+    const EpiParams &e = a.epi;
+    float *stage[2] = {(float *)buf, (float *)(buf + G_STAGE)};
+    float *stg = (float *)(buf + 2 * G_STAGE);
+    const int Me = 1 << e.a_bits, Ne = 1 << e.b_bits;
+    const int64_t K = 1ll << a.kb;
+    const int lkc = a.kb < 4 ? a.kb : 4, kc = 1 << lkc;
+    const int tx = gt % 8, ty = gt / 8;
+    if (t0 < t_end) simt_load(st, t0, 0, stage[0], gt);
+    cp_async_commit();
+    int cur = 0;
+    for (int64_t tile = t0; tile < t_end; tile += 4, cur ^= 1) {
+        const bool pre = tile + 4 < t_end;
+        if (pre) simt_load(st, tile + 4, 0, stage[cur ^ 1], gt);
+        cp_async_commit();
+        cp_async_wait<1>();  // everything but the prefetch just issued
         bar_sync(bid, 128);
-        for (int kk = 0; kk < kc; ++kk) {
-            float af[TM], bf[TN];
+        float acc[TM][TN];
 #pragma unroll
-            for (int u = 0; u < TM; ++u) af[u] = As[kk * G_PA + ty * TM + u];
+        for (int u = 0; u < TM; ++u)
 #pragma unroll
-            for (int v = 0; v < TN; v += 4) *(float4 *)&bf[v] = *(const float4 *)&Bs[kk * G_PB + tx * TN + v];
+            for (int v = 0; v < TN; ++v) acc[u][v] = 0.f;
+        for (int64_t k0 = 0; k0 < K; k0 += kc) {
+            float *As = stage[cur], *Bs = As + G_BK * G_PA;
+            if (k0 > 0) {  // further K chunks: loaded in place, synchronously
+                bar_sync(bid, 128);
+                simt_load(st, tile, k0, stage[cur], gt);
+                cp_async_commit();
+                cp_async_wait<0>();
+                bar_sync(bid, 128);
+            }
+            for (int kk = 0; kk < kc; ++kk) {
+                float af[TM], bf[TN];
 #pragma unroll
-            for (int u = 0; u < TM; ++u)
+                for (int u = 0; u < TM; ++u) af[u] = As[kk * G_PA + ty * TM + u];
 #pragma unroll
-                for (int v = 0; v < TN; ++v) acc[u][v] = fmaf(af[u], bf[v], acc[u][v]);
+                for (int v = 0; v < TN; v += 4) *(float4 *)&bf[v] = *(const float4 *)&Bs[kk * G_PB + tx * TN + v];
+#pragma unroll
+                for (int u = 0; u < TM; ++u)
+#pragma unroll
+                    for (int v = 0; v < TN; ++v) acc[u][v] = fmaf(af[u], bf[v], acc[u][v]);
+            }
         }
+#pragma unroll
+        for (int u = 0; u < TM; ++u)
+#pragma unroll
+            for (int v = 0; v < TN; v += 4)
+                *(float4 *)&stg[(ty * TM + u) * G_PS + tx * TN + v] =
+                    make_float4(acc[u][v], acc[u][v + 1], acc[u][v + 2], acc[u][v + 3]);
+        bar_sync(bid, 128);
+        const int64_t rt = tile / st.col_tiles, ct = tile - rt * st.col_tiles;
+        epi_readout(tb, stg, e, tile_base(e, (uint64_t)rt, (uint64_t)ct), Me * Ne, gt, 128, st.gmode);
         bar_sync(bid, 128);
     }
-#pragma unroll
-    for (int u = 0; u < TM; ++u)
-#pragma unroll
-        for (int v = 0; v < TN; v += 4)
-            *(float4 *)&stg[(ty * TM + u) * G_PS + tx * TN + v] =
-                make_float4(acc[u][v], acc[u][v + 1], acc[u][v + 2], acc[u][v + 3]);
-    bar_sync(bid, 128);
-    epi_readout(tb, stg, e, *base_slot, Me * Ne, gt, 128, st.gmode);
-    bar_sync(bid, 128);
+    cp_async_wait<0>();
 }
 
 // Shared control block of the CTA (after the ring).
@@ -340,9 +382,14 @@ __global__ void __launch_bounds__(BT, 1)
             if (warp >= 2) ingest_range(ing[item.idx], tid - 64, EPI);
         } else if (run && steps[item.idx].klass != KC_UMMA) {
             if (warp >= 2) {
-                const int g = (warp - 2) >> 2;
-                for (int64_t t = item.tile + g; t < item.tile + item.count; t += 4)
-                    simt_tile(steps[item.idx], &tables[item.idx], t, ring + g * G_BYTES, 2 + g, (tid - 64) & 127);
+                const int g = (warp - 2) >> 2, gt = (tid - 64) & 127;
+                uint8_t *buf = ring + g * G_BYTES;
+                // the tables sit in shared memory while the group uses them
+                EpiTables *tb = (EpiTables *)(buf + G_TABLES);
+                const uint4 *src = (const uint4 *)&tables[item.idx];
+                for (int i = gt; i < (int)(sizeof(EpiTables) / 16); i += 128) ((uint4 *)tb)[i] = src[i];
+                bar_sync(2 + g, 128);
+                simt_range(steps[item.idx], tb, item.tile + g, item.tile + item.count, buf, 2 + g, gt);
             }
         } else if (run) {
             const BStep &st = steps[item.idx];
@@ -670,14 +717,15 @@ tqc_status build_batch(Plan *const *plans, void *const *outs, int n, Batch *b) {
                 bs.bres = bs.k_blocks == 1 && bs.col_tiles == 1;
                 if (umma_make_maps(sp.prec, bs.a, bs.bn, bs.maps) != cudaSuccess)
                     return fail(TQC_ERR_CUDA, "batch: tensor map of plan " + std::to_string(pi));
-                per_item = 16;
             } else {
                 bs.bn = 64;
                 bs.col_tiles = (int64_t)1 << (sp.nb - bs.a.epi.b_bits);
                 bs.gmode = gather_mode(bs.a.epi.lowCc);
-                per_item = 16;
             }
             const int64_t n_tiles = row_tiles * bs.col_tiles;
+            // items of 16 tiles, larger for large steps (fewer pipeline drains),
+            // still about two per SM
+            per_item = std::min<int64_t>(128, std::max<int64_t>(16, n_tiles / (2 * (int64_t)sm_count()) / 4 * 4));
             const int64_t n_step_items = (n_tiles + per_item - 1) / per_item;
             bs.dep[0] = counter_of[sp.a];
             bs.need[0] = tiles_of[sp.a];
