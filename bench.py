@@ -11,6 +11,7 @@ CUDA-core form.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
   python bench.py --workload qaoa48|grid64   (tensor-bound bins, one JSON line)
+  python bench.py --hss | --planner-eval      (heavy state selection; learned planner)
 
 Under torchrun each rank reconstructs its own network instance (weak
 scaling, no collective on the data path); rank 0 prints one JSON line.
@@ -57,6 +58,9 @@ def parse():
                     help="qaoa48 / grid64: time one bin of 2^24 states of the tensor-bound networks instead")
     ap.add_argument("--mem-budget-gb", type=float, default=32.0,
                     help="device memory budget of the qaoa48 / grid64 plans (forces slicing)")
+    ap.add_argument("--hss", action="store_true",
+                    help="instead: heavy state selection on GHZ / W / Regular / Supremacy circuits (n = 20)")
+    ap.add_argument("--hss-states", type=int, default=256)
     ap.add_argument("--planner-eval", action="store_true",
                     help="instead: learned vs greedy vs exhaustive planner on 48-qubit QAOA bins")
     ap.add_argument("--pe-train", type=int, default=40)
@@ -341,6 +345,57 @@ def run_workload(args):
     return 0
 
 
+def run_hss(args):
+    """Heavy state selection (§IV) on the circuit families of §VII (n = 20,
+    3 subcircuits, exact tensors): device norms and selection, the selected
+    network gathered on the device, then the ordinary contraction of the
+    product states.  Reports the paper's metrics (P_HSS, r_{P,HSS},
+    r_|HSS|, eta_HSS) against the uncut circuit's statevector."""
+    import torch
+    from gen import statevector as sv, workloads
+    from paper_2502_03445_gb300 import tqc
+    torch.cuda.set_device(0)
+    rows = {}
+    for fam in workloads.HSS_FAMILIES:
+        net, (n, gates) = workloads.hss_circuit(fam, 20)
+        psi = sv.simulate(n, gates)
+        p_true = np.abs(psi) ** 2
+        h = tqc.Network(net)
+        zp = tqc.Plan(h, free_qubits=[])               # total mass of the full network
+        z = zp.contract(torch.empty(1, dtype=torch.float64, device="cuda"), want_z=True)
+        zp.close()
+        times = []
+        for rep in range(args.warmup + args.steps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            sel, n_states = h.hss_select(args.hss_states)
+            sub = h.select(sel)
+            plan = tqc.Plan(sub, precision=args.precision, flags=tqc.FLAG_NO_RENORM)
+            out = torch.empty(plan.out_elems, dtype=torch.float64, device="cuda")
+            plan.contract(out)
+            p_hss = float(out.sum().item()) / z
+            t = time.perf_counter() - t0
+            if rep >= args.warmup:
+                times.append(t)
+            plan.close()
+            sub.close()
+        h.close()
+        top = np.sort(p_true)[::-1][:n_states]
+        r_size = n_states / float(1 << n)
+        rows[fam] = {"cuts": net.n_cuts, "n_states": n_states, "selected_per_subcircuit": [len(x) for x in sel],
+                     "P_HSS": p_hss, "P_HSS_max": float(top.sum()), "r_P_HSS": p_hss / float(top.sum()),
+                     "r_size": r_size, "eta_HSS": p_hss / r_size, "ms": 1e3 * float(np.median(times))}
+    ms = sum(r["ms"] for r in rows.values())
+    line = {"metric": "heavy-state reconstruction: selected states per second (norms, selection, gather, contract)",
+            "value": sum(r["n_states"] for r in rows.values()) / (ms / 1e3), "unit": "states/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "dtype": args.precision, "data": "synthetic (seeded circuits, exact subcircuit tensors)",
+            "config": {"workload": f"GHZ / W / Regular / Supremacy, n = 20, 3 subcircuits, s_max = {args.hss_states}"},
+            "families": rows}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_planner_eval(args):
     """The learned planner on its configuration: 48-qubit QAOA p=1 bins of
     2^24 states (16-24 cuts, subcircuits <= 16 qubits, sliced to the memory
@@ -443,6 +498,8 @@ def main():
         return run_batch(args)
     if args.planner_eval:
         return run_planner_eval(args)
+    if args.hss:
+        return run_hss(args)
     if args.workload != "grid30":
         return run_workload(args)
     ws, rank, local = dist_env()

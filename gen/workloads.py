@@ -148,6 +148,33 @@ def batch_recipe(count: int = 256, n_lo: int = 16, n_hi: int = 28, seed0: int = 
     return nets, redraws
 
 
+HSS_FAMILIES = ("ghz", "w", "regular", "supremacy")
+
+
+def hss_circuit(family: str, n: int = 20, m: int = 3, instance: int = 0):
+    """The circuit families the paper evaluates heavy state selection on
+    (§VII-B): GHZ, W, QAOA p=1 on a random 3-regular graph ("Regular") and a
+    grid random circuit ("Supremacy", depth 5 on a rows x 5 grid), cut by the
+    annealed gate partition into ``m`` subcircuits of width <= 13, with exact
+    tensors.  Returns (network, (n, gates))."""
+    seed = 1000 * 6 + 10 * HSS_FAMILIES.index(family) + instance
+    if family == "ghz":
+        n, gates = circuits.ghz(n)
+    elif family == "w":
+        n, gates = circuits.w_state(n)
+    elif family == "regular":
+        n, gates = circuits.qaoa_regular(n, seed)
+    elif family == "supremacy":
+        n, gates = circuits.grid(n // 5, 5, 5, seed)
+    else:
+        raise ValueError(family)
+    part = cutter.anneal_partition(n, gates, m, 13, seed=seed + 5 + m, iters=4000)
+    cc = cutter.cut_circuit(n, gates, part)
+    net = tensors.exact_network(cc)
+    net.meta.update({"workload": f"hss-{family}", "circuit": f"{family} n={n}, {m} subcircuits, {cc.n_cuts} cuts"})
+    return net, (n, gates)
+
+
 def random_cut_circuit(seed: int, n: int, depth: int, n_sub: int, family: str = "line"):
     """A small random circuit cut into ``n_sub`` contiguous qubit groups."""
     rng = np.random.Generator(np.random.PCG64(seed))

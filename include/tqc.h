@@ -316,6 +316,34 @@ TQC_API tqc_status tqc_plan_candidates(tqc_net_t net, const tqc_plan_opts *opts,
                                        int32_t *n_out);
 
 /* Thread-local description of the last error ("" if none). */
+/*
+ * Heavy state selection (§IV, Alg. heavy_state_selection): reconstruct only
+ * the product of a few heavy output states per subcircuit.
+ */
+/* The L2 norm over all cut assignments of every output state of subcircuit
+ * `sub`: d_norms[i] = sqrt(sum_e T_sub[e][i]^2), i in [0, 2^{n_out}).
+ * d_norms: device, FP64, 2^{n_out} entries, caller-owned; stream-ordered. */
+TQC_API tqc_status tqc_hss_norms(tqc_net_t net, int32_t sub, double *d_norms, void *cuda_stream);
+/* Select heavy states: norms on the device, then every subcircuit is seeded
+ * with its heaviest state and states are added in descending norm (ties:
+ * lower subcircuit, then lower index) while the product of the per-subcircuit
+ * counts is below s_max.  Out (host): counts[m]; states (capacity
+ * states_cap) = each subcircuit's selected state indices, ascending,
+ * concatenated in subcircuit order; *n_states = the product of the counts.
+ * Synchronous.  TQC_ERR_INVALID if states_cap is too small. */
+TQC_API tqc_status tqc_hss_select(tqc_net_t net, int64_t s_max, int32_t *counts, int32_t *states,
+                                  int64_t states_cap, int64_t *n_states);
+/* A new network whose subcircuit j keeps only the output states
+ * states[o_j .. o_j + counts[j]) (ascending indices into its 2^{n_out} states;
+ * o_j = counts[0] + ... + counts[j-1]), padded with zero rows to 2^{k_j},
+ * k_j = ceil(log2 counts[j]).  Its outputs are the selection indices:
+ * subcircuit j's k_j bits follow those of subcircuits 0..j-1 (at least one
+ * bit in total).  Cuts and roles are unchanged; the rows are gathered on the
+ * device (synchronous).  Contract it with TQC_FLAG_NO_RENORM and divide by
+ * the source network's total mass to get the product states' probabilities;
+ * padded entries are zero.  Destroy with tqc_destroy. */
+TQC_API tqc_status tqc_network_select(tqc_net_t net, const int32_t *counts, const int32_t *states, tqc_net_t *out);
+
 TQC_API const char *tqc_last_error(void);
 
 #ifdef __cplusplus

@@ -32,7 +32,8 @@ EXPORTS = ["tqc_network_create", "tqc_network_upload", "tqc_destroy", "tqc_plan_
            "tqc_contract_noalloc", "tqc_noalloc_scratch_bytes", "tqc_costmodel_create", "tqc_costmodel_destroy",
            "tqc_costmodel_params", "tqc_costmodel_set_params", "tqc_costmodel_grad", "tqc_costmodel_train",
            "tqc_costmodel_predict", "tqc_costmodel_save", "tqc_costmodel_load", "tqc_plan_features",
-           "tqc_plan_candidates", "tqc_batch_status", "tqc_batch_inject_stall"]
+           "tqc_plan_candidates", "tqc_batch_status", "tqc_batch_inject_stall", "tqc_hss_norms", "tqc_hss_select",
+           "tqc_network_select"]
 PLAN_FEATURES = 32
 
 
@@ -104,6 +105,11 @@ def lib():
         L.tqc_plan_candidates.argtypes = [vp, ctypes.POINTER(PlanOpts), i32, vp, i32p]
         L.tqc_batch_status.argtypes = [vp]
         L.tqc_batch_inject_stall.argtypes = [i32]
+        L.tqc_hss_norms.argtypes = [vp, i32, vp, vp]
+        L.tqc_hss_select.argtypes = [vp, ctypes.c_int64, vp, vp, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]
+        L.tqc_network_select.argtypes = [vp, vp, vp, ctypes.POINTER(vp)]
+        for name in ["tqc_hss_norms", "tqc_hss_select", "tqc_network_select"]:
+            getattr(L, name).restype = ctypes.c_int
         for name in ["tqc_batch_status", "tqc_batch_inject_stall", "tqc_costmodel_create", "tqc_costmodel_destroy",
                      "tqc_costmodel_params",
                      "tqc_costmodel_set_params", "tqc_costmodel_grad", "tqc_costmodel_train",
@@ -159,6 +165,43 @@ class Network:
         self.handle = h
         self.dtype = dtype
         self.plans = []
+
+    @classmethod
+    def _wrap(cls, handle, n_qubits, m, dtype):
+        self = cls.__new__(cls)
+        self.handle, self.n_qubits, self.m, self.dtype, self.plans, self._keep = handle, n_qubits, m, dtype, [], None
+        return self
+
+    def hss_norms(self, sub, out, stream=None):
+        """L2 norms over the cut assignments of every output state of
+        subcircuit ``sub`` into ``out`` (CUDA float64 tensor)."""
+        assert out.is_cuda and out.is_contiguous()
+        _check(lib().tqc_hss_norms(self.handle, int(sub), ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
+
+    def hss_select(self, s_max):
+        """Heavy states: (list of ascending state arrays per subcircuit,
+        product of the counts)."""
+        counts = np.zeros(self.m, np.int32)
+        cap = 1 << 22
+        states = np.zeros(cap, np.int32)
+        n = ctypes.c_int64()
+        _check(lib().tqc_hss_select(self.handle, ctypes.c_int64(int(s_max)), counts.ctypes.data, states.ctypes.data,
+                                    ctypes.c_int64(cap), ctypes.byref(n)))
+        out, off = [], 0
+        for c in counts:
+            out.append(states[off:off + c].copy())
+            off += c
+        return out, n.value
+
+    def select(self, selection):
+        """The network restricted to the product of the selected states
+        (see tqc_network_select); its outputs are the selection indices."""
+        counts = np.ascontiguousarray([len(x) for x in selection], np.int32)
+        states = np.ascontiguousarray(np.concatenate([np.asarray(x, np.int64) for x in selection]), np.int32)
+        h = ctypes.c_void_p()
+        _check(lib().tqc_network_select(self.handle, counts.ctypes.data, states.ctypes.data, ctypes.byref(h)))
+        kb = [int(np.ceil(np.log2(c))) if c > 1 else 0 for c in counts]
+        return Network._wrap(h, max(1, sum(kb)), self.m, self.dtype)
 
     def upload(self, sub, host_array, stream=None):
         arr = np.ascontiguousarray(host_array)
