@@ -196,9 +196,11 @@ TQC_API tqc_status tqc_contract(tqc_plan_t plan, const uint8_t *fixed_bits, void
 
 /*
  * End-to-end form with host buffers: copies every subcircuit tensor from
- * host_tensors[j] (dtype in_dtype, NULL = unchanged) to the device, runs
- * tqc_contract into a plan-owned device buffer, copies the 2^F results into
- * host_out (out_dtype) and synchronises the stream.
+ * host_tensors[j] (dtype in_dtype, NULL = unchanged) to the device and runs
+ * tqc_contract.  When host_out is pinned host memory mapped into the device's
+ * address space, the last kernel stores the 2^F results (out_dtype) straight
+ * into it; otherwise they go to a plan-owned device buffer and are copied
+ * into host_out.  Synchronises the stream.
  */
 TQC_API tqc_status tqc_contract_host(tqc_plan_t plan, const void *const *host_tensors, int32_t in_dtype,
                                      void *host_out, int32_t out_dtype, double *z_out, void *cuda_stream);

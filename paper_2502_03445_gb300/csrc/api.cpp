@@ -252,6 +252,23 @@ tqc_status tqc_contract_host(tqc_plan_t plan, const void *const *host_tensors, i
                 p.net->version++;
             }
     int64_t ob = p.out_elems() * (out_dtype == TQC_F64 ? 8 : 4);
+    // Pinned host memory mapped into the device's address space (Grace's
+    // memory over NVLink-C2C): the last kernel stores the probabilities there
+    // directly, with no device copy of the result and no separate download.
+    {
+        cudaPointerAttributes at;
+        if (cudaPointerGetAttributes(&at, host_out) == cudaSuccess && at.type == cudaMemoryTypeHost &&
+            at.devicePointer != nullptr) {
+            tqc_status st = exec_contract(&p, nullptr, at.devicePointer, out_dtype, nullptr, stream);
+            if (st != TQC_OK) return st;
+            cudaError_t e = cudaSuccess;
+            if (z_out) e = cudaMemcpyAsync(z_out, p.d_zinfo, sizeof(double), cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) return fail(TQC_ERR_CUDA, std::string("result: ") + cudaGetErrorString(e));
+            return TQC_OK;
+        }
+        cudaGetLastError();
+    }
     if (p.d_hostout_bytes < ob) {
         if (p.d_hostout) cudaFree(p.d_hostout);
         p.d_hostout = nullptr;
