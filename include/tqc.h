@@ -51,7 +51,7 @@ typedef enum {
     TQC_ERR_OOM = 2,          /* device or host allocation failed, or budget too small */
     TQC_ERR_CUDA = 3,         /* a CUDA call failed (message holds cudaGetErrorString) */
     TQC_ERR_TIMEOUT = 4,      /* a bounded device-side wait gave up */
-    TQC_ERR_UNSUPPORTED = 5   /* valid request outside what this build supports */
+    TQC_ERR_UNSUPPORTED = 5   /* valid request outside what the library supports */
 } tqc_status;
 
 /* element types of tensors and outputs */

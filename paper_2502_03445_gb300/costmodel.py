@@ -38,7 +38,7 @@ def collect(handle: "tqc.Network", precision="auto", free_qubits=None, max_candi
 
     Returns a list of records ``{"order", "features", "seconds",
     "predicted_s", "flops"}`` (``predicted_s`` is the analytic model's
-    estimate, the planner's own judge).  ``mem_budget`` (device bytes, 0 =
+    estimate, the planner's own model).  ``mem_budget`` (device bytes, 0 =
     unlimited) slices every candidate as tqc_plan would.  Candidates whose
     analytic estimate exceeds ``window`` times the best one are not timed:
     the learned planner never ranks them either (see tqc_plan)."""

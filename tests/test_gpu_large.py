@@ -21,8 +21,8 @@ rounding error.  Bound per state: n_steps * 2^-12 * s.  Each step rounds
 its products to about 2^-16 relative (split BF16; 2^-24 for FP32) and
 accumulates K terms in FP32, whose randomly signed rounding errors grow like
 sqrt(K) * 2^-24 <= 2^-13 for K <= 2^22; the FP64 slice sum adds nothing
-visible.  The task's absolute FP32 gate (1e-5 per probability) is asserted
-as well."""
+visible.  The absolute FP32 tolerance (1e-5 per probability) is asserted as
+well."""
 import functools
 
 import numpy as np

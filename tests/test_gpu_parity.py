@@ -1,6 +1,6 @@
 """CUDA path vs the FP64 oracle, element by element, through the C ABI.
 
-Tolerances (stated by the benchmark spec for this path): FP32 form <= 1e-5 absolute per
+Tolerances: FP32 form <= 1e-5 absolute per
 probability; tensor-core forms <= 1e-3 total variation.  Both are also
 checked relative to the largest probability, since probabilities are ~2^-n.
 All sizes are powers of two (dimension 2 outputs, dimension 4 cuts), so the
