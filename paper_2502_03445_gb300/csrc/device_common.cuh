@@ -332,16 +332,16 @@ __device__ __forceinline__ void store_vals(const EpiParams &e, uint64_t off, con
     }
 }
 
-// Direct stores of 32 consecutive accumulator columns of one row, VW at a
-// time: run j (j = 0, VW, 2 VW, ...) goes to o + x_j, where x_j is the
+// Direct stores of NV (32 or 16) consecutive accumulator columns of one
+// row, VW at a time: run j (j = 0, VW, 2 VW, ...) goes to o + x_j, where x_j is the
 // deposit of j into the result bits of the column index; the next deposit
 // is ((x | ~m) + 1) & m with m = those bits minus the VW-run bits.
-template <int MODE, int VW>
+template <int MODE, int VW, int NV = 32>
 __device__ __forceinline__ void direct_run32(const EpiParams &e, uint64_t o, uint64_t m, const uint32_t *r, float sf,
                                              double sd) {
     uint64_t x = 0;
 #pragma unroll
-    for (int j = 0; j < 32; j += VW) {
+    for (int j = 0; j < NV; j += VW) {
         float v[VW];
 #pragma unroll
         for (int i = 0; i < VW; ++i) v[i] = __uint_as_float(r[j + i]);
@@ -350,26 +350,27 @@ __device__ __forceinline__ void direct_run32(const EpiParams &e, uint64_t o, uin
     }
 }
 
-template <int MODE>
+template <int MODE, int NV = 32>
 __device__ __forceinline__ void direct_run32_vw(const EpiParams &e, int vw, uint64_t o, uint64_t m, const uint32_t *r,
                                                 float sf, double sd) {
-    if (vw == 4) direct_run32<MODE, 4>(e, o, m, r, sf, sd);
-    else if (vw == 2) direct_run32<MODE, 2>(e, o, m, r, sf, sd);
-    else direct_run32<MODE, 1>(e, o, m, r, sf, sd);
+    if (vw == 4) direct_run32<MODE, 4, NV>(e, o, m, r, sf, sd);
+    else if (vw == 2) direct_run32<MODE, 2, NV>(e, o, m, r, sf, sd);
+    else direct_run32<MODE, 1, NV>(e, o, m, r, sf, sd);
 }
 
-// Mode dispatch, once per 32 values.
+// Mode dispatch, once per NV values.
+template <int NV = 32>
 __device__ __forceinline__ void direct_run32_any(const EpiParams &e, int vw, uint64_t o, uint64_t m, const uint32_t *r,
                                                  float sf, double sd) {
     switch (e.mode) {
-        case EPI_F32: direct_run32_vw<EPI_F32>(e, vw, o, m, r, sf, sd); break;
-        case EPI_TF32: direct_run32_vw<EPI_TF32>(e, vw, o, m, r, sf, sd); break;
-        case EPI_BF16: direct_run32_vw<EPI_BF16>(e, vw, o, m, r, sf, sd); break;
-        case EPI_BF16X2: direct_run32_vw<EPI_BF16X2>(e, vw, o, m, r, sf, sd); break;
-        case EPI_F64_SET: direct_run32_vw<EPI_F64_SET>(e, vw, o, m, r, sf, sd); break;
-        case EPI_F64_ADD: direct_run32_vw<EPI_F64_ADD>(e, vw, o, m, r, sf, sd); break;
-        case EPI_OUT_F32: direct_run32_vw<EPI_OUT_F32>(e, vw, o, m, r, sf, sd); break;
-        case EPI_OUT_F64: direct_run32_vw<EPI_OUT_F64>(e, vw, o, m, r, sf, sd); break;
+        case EPI_F32: direct_run32_vw<EPI_F32, NV>(e, vw, o, m, r, sf, sd); break;
+        case EPI_TF32: direct_run32_vw<EPI_TF32, NV>(e, vw, o, m, r, sf, sd); break;
+        case EPI_BF16: direct_run32_vw<EPI_BF16, NV>(e, vw, o, m, r, sf, sd); break;
+        case EPI_BF16X2: direct_run32_vw<EPI_BF16X2, NV>(e, vw, o, m, r, sf, sd); break;
+        case EPI_F64_SET: direct_run32_vw<EPI_F64_SET, NV>(e, vw, o, m, r, sf, sd); break;
+        case EPI_F64_ADD: direct_run32_vw<EPI_F64_ADD, NV>(e, vw, o, m, r, sf, sd); break;
+        case EPI_OUT_F32: direct_run32_vw<EPI_OUT_F32, NV>(e, vw, o, m, r, sf, sd); break;
+        case EPI_OUT_F64: direct_run32_vw<EPI_OUT_F64, NV>(e, vw, o, m, r, sf, sd); break;
         default: break;
     }
 }

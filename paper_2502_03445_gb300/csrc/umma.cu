@@ -171,6 +171,15 @@ __device__ __forceinline__ bool epi_barrier_or(int nthreads, bool pred) {
     return r != 0;
 }
 
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
@@ -365,6 +374,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         }
         const double sd = (e.mode == EPI_OUT_F32 || e.mode == EPI_OUT_F64) ? e.zinfo[1] : 1.0;
         const float sf = (float)sd;
+        // column 16 of a chunk (chunks start at multiples of 32, so its
+        // deposit adds to the chunk's: the bits are disjoint)
+        const uint64_t off16 = pdep64(16, colmask);
         int64_t lt = 0;
         for (int64_t tile = blockIdx.x; tile < P.n_tiles; tile += gridDim.x, ++lt) {
             const int acc = (int)(lt & 1);
@@ -376,18 +388,20 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             const uint64_t ct = (uint64_t)(tile - (int64_t)rt * P.col_tiles);
             // sub-tile column index ct * SUBS + h: the h bits are the lowest bits of highC (in coff)
             const uint64_t base = warp_pdep64(rt, e.highR) | warp_pdep64(ct * SUBS, e.highC);
-            // one 32-column chunk at a time (registers); the accumulator is
-            // freed once the last chunk has been loaded
+            // one half chunk (16 columns) at a time: 16 values in registers
+            // keep the warp under its 96-register share without spills; the
+            // accumulator is freed once the last half has been loaded
 #pragma unroll
-            for (int c = 0; c < CH; ++c) {
-                uint32_t r[32];
-                tmem_ld32(tmem_base + ((uint32_t)(lane_grp * 32) << 16) + (uint32_t)(acc * BN + (q + 4 * c) * 32), r);
-                if (c == CH - 1) {
+            for (int c = 0; c < 2 * CH; ++c) {
+                uint32_t r[16];
+                tmem_ld16(tmem_base + ((uint32_t)(lane_grp * 32) << 16) +
+                              (uint32_t)(acc * BN + (q + 4 * (c >> 1)) * 32 + (c & 1) * 16), r);
+                if (c == 2 * CH - 1) {
                     tc_fence_before();
                     __syncwarp();
                     if (lane == 0) mbar_arrive(&tempty[acc]);
                 }
-                direct_run32_any(e, vw, base + grow + coff[c], mstep, r, sf, sd);
+                direct_run32_any<16>(e, vw, base + grow + coff[c >> 1] + ((c & 1) ? off16 : 0), mstep, r, sf, sd);
             }
         }
     } else {
