@@ -288,6 +288,25 @@ def tensor_peak(prec, bf16):
     return bf16, "measured bf16 burst"
 
 
+def path_roofline(steps, n_slices, hbm, bf16):
+    """Roofline time of the whole plan in ms: for every step the larger of
+    its algorithmic bytes over HBM bandwidth and its algorithmic flops over
+    the tensor peak of its precision (CUDA-core steps: bytes only), summed
+    over the steps and repeated per slice.  Intermediates count 4 bytes per
+    element; the final step writes FP32 once, or reads and writes the FP64
+    accumulator once per slice when the plan is sliced."""
+    t = 0.0
+    for i, st in enumerate(steps):
+        last = i == len(steps) - 1
+        tb = step_bytes(st, (16 if n_slices > 1 else 4) if last else 4) / (hbm * 1e9)
+        tf = 0.0
+        if st["class"] == "tcgen05":
+            pk, _ = tensor_peak(st["prec"], bf16)
+            tf = 2.0 * 2 ** (st["log2_m"] + st["log2_n"] + st["log2_k"]) / (pk * 1e12)
+        t += max(tb, tf)
+    return t * n_slices * 1e3
+
+
 def run_workload(args):
     """One 2^24-state bin of the 48-qubit QAOA network or of the 64-qubit
     grid shape, sliced to the memory budget: these plans end in tensor-bound
@@ -318,6 +337,9 @@ def run_workload(args):
                       f"tile {st['tile']})",
             "algorithmic_flops_per_launch": alg, "mean_launch_ms": step_ms[top], "step_ms": step_ms,
             "tensor_pipe_issue_frac_of_bf16": achieved * (3 if st["prec"] == "bf16x3" else 1) / bf16}
+    hbm = peaks()[0]
+    roof["path_roofline_ms"] = path_roofline(desc["steps"], info["n_slices"], hbm, bf16)
+    roof["path_frac"] = roof["path_roofline_ms"] / ms
     # sampled check and CPU baseline: oracle B, one state at a time
     rng = np.random.Generator(np.random.PCG64(5))
     states = [int(x) for x in rng.integers(0, 1 << net.n_qubits, size=4)]
@@ -571,6 +593,12 @@ def main():
     roof["algorithmic_bytes_per_launch"] = byt
     roof["mean_launch_ms"] = step_ms[top]
     roof["step_ms"] = step_ms
+    # the whole plan against its roofline, and the plan-independent floor
+    # (the FP32 output written once and the FP64 node tensors read once)
+    roof["path_roofline_ms"] = path_roofline(desc["steps"], 1, hbm, bf16)
+    roof["path_frac"] = roof["path_roofline_ms"] / ms
+    in_bytes = sum(8 * nd.tensor().size for nd in net.nodes)
+    roof["floor_ms"] = (4 * plan.out_elems + in_bytes) / (hbm * 1e9) * 1e3
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",

@@ -162,14 +162,13 @@ __device__ __forceinline__ void mma_issue(int prec, uint32_t d, uint64_t a, uint
             "l"(a), "l"(b), "r"(idesc), "r"(acc));
 }
 
-__device__ __forceinline__ void tmem_load32(uint32_t taddr, uint32_t (&r)[32]) {
+// 16 accumulator columns of the warp's 32 TMEM lanes (16 values in
+// registers keep the epilogue warps under their 96-register share)
+__device__ __forceinline__ void tmem_load16(uint32_t taddr, uint32_t (&r)[16]) {
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
         : "r"(taddr));
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
@@ -514,11 +513,13 @@ __global__ void __launch_bounds__(BT, 1)
                         __syncwarp();
                         if (lane == 0) bmbar_arrive(&ctl->tempty[acc]);
                     }
-                    for (int c = 0; c < nch; ++c) {
-                        const int col0 = q * 32 + 128 * c;
-                        uint32_t r[32];
-                        tmem_load32(tmem + ((uint32_t)(lane_grp * 32) << 16) + (uint32_t)(acc * 256 + col0), r);
-                        if (c == nch - 1) {
+                    // in halves of 16 columns: j0 is a multiple of 16, so the
+                    // deposits of j0 and of j < 16 add (disjoint bits)
+                    for (int c = 0; c < 2 * nch; ++c) {
+                        const int col0 = q * 32 + 128 * (c >> 1) + 16 * (c & 1);
+                        uint32_t r[16];
+                        tmem_load16(tmem + ((uint32_t)(lane_grp * 32) << 16) + (uint32_t)(acc * 256 + col0), r);
+                        if (c == 2 * nch - 1) {
                             tc_before();
                             __syncwarp();
                             if (lane == 0) bmbar_arrive(&ctl->tempty[acc]);
@@ -527,10 +528,10 @@ __global__ void __launch_bounds__(BT, 1)
                         const uint64_t o = base + grow + pdep64((uint64_t)j0, colmask) +
                                            pdep64((uint64_t)(col0 / 64), e.highC);
                         if (full) {
-                            direct_run32_any(e, vw, o, mstep, r, sf, sd);
+                            direct_run32_any<16>(e, vw, o, mstep, r, sf, sd);
                         } else if (row < Me && j0 < Ne) {
                             uint64_t x = 0;
-                            const int nc = Ne - j0 < 32 ? Ne - j0 : 32;
+                            const int nc = Ne - j0 < 16 ? Ne - j0 : 16;
                             for (int j = 0; j < nc; ++j) {
                                 const float v = __uint_as_float(r[j]);
                                 store_run_f32(e, o + x, &v, 1, sd);
