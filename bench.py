@@ -145,10 +145,13 @@ def step_flops(st):
 
 def traffic_record(kernel):
     """dram read+write bytes per launch from the committed ncu summary, or
-    None when the kernel source changed since the capture."""
+    None when the kernel's sources (its .cu file and the shared epilogue
+    header) changed since the capture."""
     import hashlib
     path = os.path.join(ROOT, "profiles", f"{kernel}_traffic.md")
-    src = os.path.join(ROOT, "paper_2502_03445_gb300", "csrc", "umma.cu" if kernel.startswith("umma") else "simt.cu")
+    csrc = os.path.join(ROOT, "paper_2502_03445_gb300", "csrc")
+    srcs = [os.path.join(csrc, "umma.cu" if kernel.startswith("umma") else "simt.cu"),
+            os.path.join(csrc, "device_common.cuh")]
     try:
         rec = {}
         with open(path) as f:
@@ -156,7 +159,7 @@ def traffic_record(kernel):
                 if ":" in line and line.startswith("- "):
                     k, v = line[2:].split(":", 1)
                     rec[k.strip()] = v.strip()
-        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        h = hashlib.sha256(b"".join(open(f, "rb").read() for f in srcs)).hexdigest()[:16]
         if rec.get("source_sha256_16") != h:
             return None
         return float(rec["dram_bytes_per_full_launch"])
