@@ -215,6 +215,65 @@ int default_step_tile(const StepPlan &st, int out_esize) {
     return (st.mb >= 7 && st.nb >= 7) ? SIMT_128x128 : (st.mb >= 7 && st.nb >= 6 ? SIMT_128x64 : SIMT_64x64);
 }
 
+// K split of a final tensor-core step in the deep form.  T tiles on S SMs
+// take ceil(T / S) waves of the whole K loop, so when T is not a multiple of
+// S the last wave leaves SMs idle (512 tiles on 152 SMs: 3.37 waves take 4).
+// Running k ranges of K as separate units evens the waves; each unit stores
+// an FP32 partial and one reduce pass sums them in FP64.  Time model, in
+// k-block units of about a microsecond: ceil(T k / S) (k_blocks / k + 4)
+// (4 = pipeline fill and epilogue per unit), plus the reduce's bytes at HBM
+// speed.  The smallest k within 2% of the best is taken, with at least 16
+// k-blocks per range and the partials within max_part_bytes.
+int step_ksplit(const StepPlan &st, int64_t out_elems, int64_t max_part_bytes) {
+    if (!st.final || st.klass != KC_UMMA) return 1;
+    if (st.tile != UMMA_128x128_DEEP && st.tile != UMMA_128x256_DEEP) return 1;
+    const int lbn = st.tile == UMMA_128x256_DEEP ? 8 : 7;
+    const int lbk = st.prec == TQC_PREC_TF32 ? 5 : 6;  // 128-byte k-blocks
+    if (st.mb < 7 || st.nb < lbn || st.kb < lbk) return 1;
+    const int64_t tiles = ((int64_t)1 << (st.mb - 7)) << (st.nb - lbn);
+    const int64_t kblocks = (int64_t)1 << (st.kb - lbk);
+    const int64_t sms = sm_count();
+    constexpr int KMAX = 16;
+    double cost[KMAX + 1];
+    int kmax = 1;
+    for (int k = 1; k <= KMAX; ++k) {
+        if (k > 1 && (kblocks / k < 16 || (int64_t)k * out_elems * 4 > max_part_bytes)) break;
+        const double waves = (double)((tiles * k + sms - 1) / sms);
+        cost[k] = waves * ((double)kblocks / k + 4.0) * 1e-6 +
+                  (k > 1 ? (4.0 * k + 16.0) * (double)out_elems / 6.8e12 + 5e-6 : 0.0);
+        kmax = k;
+    }
+    double best = cost[1];
+    for (int k = 2; k <= kmax; ++k) best = std::min(best, cost[k]);
+    for (int k = 1; k <= kmax; ++k)
+        if (cost[k] <= best * 1.02) return k;
+    return 1;
+}
+
+// Sets every step's K split for its current tile and sizes the partials'
+// buffer (allocated once, grown if the autotuner picked a tile that splits
+// further).
+tqc_status update_ksplit(Plan *p) {
+    const int64_t cap = p->budget ? (int64_t)(p->budget / 16) : ((int64_t)1 << 30);
+    int64_t need = 0;
+    for (auto &st : p->steps) {
+        st.ksplit = step_ksplit(st, p->out_elems(), cap);
+        if (st.ksplit > 1) need = std::max(need, (int64_t)st.ksplit * p->out_elems() * 4);
+    }
+    if (need > p->kpart_bytes) {
+        if (p->d_kpart) cudaFree(p->d_kpart);
+        p->d_kpart = nullptr;
+        p->kpart_bytes = 0;
+        cudaError_t e = cudaMalloc(&p->d_kpart, (size_t)need);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(TQC_ERR_OOM, "K-split partials of " + std::to_string(need) + " bytes");
+        }
+        p->kpart_bytes = need;
+    }
+    return TQC_OK;
+}
+
 IngestArgs exec_leaf_args(const Plan &p, const TensorPlan &t, int j, const uint8_t *fixed) {
     return leaf_args(p, t, j, fixed, 0, false);
 }
@@ -291,7 +350,10 @@ tqc_status exec_autotune(Plan *p, void *d_out, int out_dtype, cudaStream_t s) {
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    if (result == TQC_OK) p->tuned = 1;
+    if (result == TQC_OK) {
+        p->tuned = 1;
+        result = update_ksplit(p);
+    }
     return result;
 }
 
@@ -324,6 +386,8 @@ tqc_status exec_prepare(Plan *p) {
     for (auto &st : p->steps) {
         st.tile = default_step_tile(st, step_out_esize(*p, st));
     }
+    tqc_status kst = update_ksplit(p);
+    if (kst != TQC_OK) return kst;
     p->ready = true;
     return TQC_OK;
 }
@@ -358,7 +422,9 @@ void exec_release(Plan *p) {
     if (p->d_ws) cudaFree(p->d_ws);
     if (p->d_zws) cudaFree(p->d_zws);
     if (p->d_zinfo) cudaFree(p->d_zinfo);
-    p->d_ws = p->d_zws = nullptr;
+    if (p->d_kpart) cudaFree(p->d_kpart);
+    p->d_ws = p->d_zws = p->d_kpart = nullptr;
+    p->kpart_bytes = 0;
     p->d_zinfo = nullptr;
     p->ready = false;
 }
@@ -452,8 +518,23 @@ tqc_status exec_contract(Plan *p, const uint8_t *fixed_bits, void *d_out, int ou
                     TQC_CUDA(cudaEventCreate(&ev[1]), "event");
                     TQC_CUDA(cudaEventRecord(ev[0], s), "event record");
                 }
-                st = launch_step(*p, sp, a, d_err, s);
-                if (st != TQC_OK) return st;
+                if (sp.ksplit > 1) {
+                    // split K: FP32 partials, then one pass into the step's own output mode
+                    void *out = a.epi.out;
+                    const int mode = a.epi.mode;
+                    a.ksplit = sp.ksplit;
+                    a.split_stride = p->out_elems();
+                    a.epi.out = p->d_kpart;
+                    a.epi.mode = EPI_F32;
+                    st = launch_step(*p, sp, a, d_err, s);
+                    if (st != TQC_OK) return st;
+                    TQC_CUDA(launch_ksplit_reduce((const float *)p->d_kpart, sp.ksplit, p->out_elems(), mode, out,
+                                                  p->d_zinfo, s),
+                             "K-split reduce");
+                } else {
+                    st = launch_step(*p, sp, a, d_err, s);
+                    if (st != TQC_OK) return st;
+                }
                 if (p->profile) {
                     TQC_CUDA(cudaEventRecord(ev[1], s), "event record");
                     if (p->step_events.size() < p->steps.size()) p->step_events.resize(p->steps.size());

@@ -24,6 +24,10 @@ cudaError_t launch_ingest(const IngestArgs &g, int64_t n_dst, cudaStream_t s);
 cudaError_t launch_zfinal(const double *zslice, int n, int n_cuts, int renorm, double *zinfo, cudaStream_t s);
 cudaError_t launch_finalize(const double *acc, void *out, int out_f64, const double *zinfo, int64_t n,
                             cudaStream_t s);
+// Sum of a K-split step's FP32 partials (split s at part + s * n) into its
+// output mode (EPI_OUT_F32 / EPI_OUT_F64 / EPI_F64_SET / EPI_F64_ADD).
+cudaError_t launch_ksplit_reduce(const float *part, int ksplit, int64_t n, int mode, void *out, const double *zinfo,
+                                 cudaStream_t s);
 
 // tcgen05 step (umma.cu)
 // *_DEEP: direct epilogue and a deeper operand ring, for steps with a long K loop
@@ -42,6 +46,9 @@ int exec_epi_mode(int storage);
 // per result element its epilogue writes).
 constexpr int DEEP_MIN_LOG2_K = 12;
 int default_step_tile(const StepPlan &st, int out_esize);
+// K splits of a final tensor-core step with too few tiles to fill the GPU
+// evenly (1 = no split); max_part_bytes caps the FP32 partials it stores.
+int step_ksplit(const StepPlan &st, int64_t out_elems, int64_t max_part_bytes);
 int step_out_esize(const Plan &p, const StepPlan &st);
 double direct_store_efficiency(const EpiParams &e, int esize);
 

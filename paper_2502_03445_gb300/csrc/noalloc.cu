@@ -106,7 +106,7 @@ extern "C" tqc_status tqc_contract_noalloc(tqc_plan_t plan, const void *const *d
     Net &net = *p.net;
     void *saved_data[64];
     int saved_dtype[64];
-    int sv_tiles[64];
+    int sv_tiles[64], sv_ksplit[64];
     for (int j = 0; j < p.m; ++j) {
         saved_data[j] = net.nodes[j].d_data;
         saved_dtype[j] = net.nodes[j].dtype;
@@ -120,15 +120,19 @@ extern "C" tqc_status tqc_contract_noalloc(tqc_plan_t plan, const void *const *d
     p.z_version = 0;  // the caller's tensors: always compute the total mass
     const int sv_profile = p.profile;
     const int sv_device = net.device;
-    for (size_t i = 0; i < p.steps.size(); ++i) sv_tiles[i] = p.steps[i].tile;
+    for (size_t i = 0; i < p.steps.size(); ++i) {
+        sv_tiles[i] = p.steps[i].tile;
+        sv_ksplit[i] = p.steps[i].ksplit;
+    }
     p.d_zinfo = (double *)base;
     p.d_zws = (char *)base + zws_off;  // the per-slice masses follow the Z network buffers
     p.d_ws = (char *)base + ws_off;
     p.ready = true;
     p.profile = 0;
     net.device = dev;
-    for (auto &st : p.steps) {  // the tile rule of the allocating path
+    for (auto &st : p.steps) {  // the tile rule of the allocating path, unsplit (no partials buffer)
         st.tile = default_step_tile(st, step_out_esize(p, st));
+        st.ksplit = 1;
     }
     tqc_status st = exec_contract(&p, fixed_bits, d_out, out_dtype, nullptr, cuda_stream);
     // restore
@@ -143,6 +147,9 @@ extern "C" tqc_status tqc_contract_noalloc(tqc_plan_t plan, const void *const *d
     p.z_version = sv_zver;
     p.profile = sv_profile;
     net.device = sv_device;
-    for (size_t i = 0; i < p.steps.size(); ++i) p.steps[i].tile = sv_tiles[i];
+    for (size_t i = 0; i < p.steps.size(); ++i) {
+        p.steps[i].tile = sv_tiles[i];
+        p.steps[i].ksplit = sv_ksplit[i];
+    }
     return st;
 }

@@ -823,7 +823,8 @@ std::string plan_describe(const Plan &pl) {
            << ",\"log2_n\":" << st.nb << ",\"log2_k\":" << st.kb << ",\"class\":\""
            << (st.klass == KC_UMMA ? "tcgen05" : "simt") << "\",\"prec\":\""
            << (st.klass == KC_UMMA ? prec_name(st.prec) : "fp32") << "\",\"out_layout\":" << mode_str(p->tensors[st.c].layout)
-           << ",\"mask_r\":" << st.maskR << ",\"mask_c\":" << st.maskC << ",\"tile\":" << st.tile << "}";
+           << ",\"mask_r\":" << st.maskR << ",\"mask_c\":" << st.maskC << ",\"tile\":" << st.tile
+           << ",\"ksplit\":" << st.ksplit << "}";
     }
     os << "],\"layouts\":[";
     for (size_t i = 0; i < p->tensors.size(); ++i) os << (i ? "," : "") << mode_str(p->tensors[i].layout);
@@ -834,7 +835,8 @@ std::string plan_describe(const Plan &pl) {
     if (p->m == 1) launches += 1;
     else {
         for (int j = 0; j < p->m; ++j) launches += p->tensors[j].slice_dep ? p->n_slices() : 1;
-        for (auto &st : p->steps) launches += p->tensors[st.c].slice_dep ? p->n_slices() : 1;
+        for (auto &st : p->steps)  // a K-split step adds its reduce pass
+            launches += (p->tensors[st.c].slice_dep ? p->n_slices() : 1) * (st.ksplit > 1 ? 2 : 1);
         if (p->n_slices() > 1) launches += 1;
     }
     os << "],\"launches_per_contract\":" << launches << ",\"total_mass_launches\":" << z_launches;

@@ -216,6 +216,26 @@ __global__ void finalize_kernel(const double *acc, void *out, int out_f64, const
     }
 }
 
+// Sum of the FP32 partials of a K-split step (split s at part + s * n), in
+// FP64, stored in the step's own output mode: the scaled final output
+// (FP32 / FP64) or the FP64 slice sum (set / add).
+__global__ void ksplit_reduce_kernel(const float *part, int ksplit, int64_t n, int mode, void *out,
+                                     const double *zinfo) {
+    const double sc = (mode == EPI_OUT_F32 || mode == EPI_OUT_F64) ? zinfo[1] : 1.0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        double v = 0.0;
+        for (int s = 0; s < ksplit; ++s) v += (double)part[s * n + i];
+        switch (mode) {
+            case EPI_OUT_F32: ((float *)out)[i] = (float)(v * sc); break;
+            case EPI_OUT_F64: ((double *)out)[i] = v * sc; break;
+            case EPI_F64_SET: ((double *)out)[i] = v; break;
+            case EPI_F64_ADD: ((double *)out)[i] += v; break;
+            default: break;
+        }
+    }
+}
+
 int g_sms = 0;
 
 template <int BM, int BN, int TM, int TN>
@@ -296,6 +316,16 @@ cudaError_t launch_finalize(const double *acc, void *out, int out_f64, const dou
     int64_t blocks = std::min<int64_t>((n + 255) / 256, (int64_t)sm_count() * 32);
     if (blocks < 1) blocks = 1;
     finalize_kernel<<<(unsigned)blocks, 256, 0, s>>>(acc, out, out_f64, zinfo, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ksplit_reduce(const float *part, int ksplit, int64_t n, int mode, void *out, const double *zinfo,
+                                 cudaStream_t s) {
+    if (ksplit < 1 || n < 1) return cudaErrorInvalidValue;
+    if (mode != EPI_OUT_F32 && mode != EPI_OUT_F64 && mode != EPI_F64_SET && mode != EPI_F64_ADD)
+        return cudaErrorInvalidValue;
+    const int64_t blocks = std::min<int64_t>((n + 255) / 256, (int64_t)sm_count() * 32);
+    ksplit_reduce_kernel<<<(unsigned)blocks, 256, 0, s>>>(part, ksplit, n, mode, out, zinfo);
     return cudaGetLastError();
 }
 

@@ -99,6 +99,7 @@ struct StepPlan {
     uint64_t maskR = 0, maskC = 0;  // result-layout bits of row / column index bits
     bool final = false;
     int tile = 0;                 // tile configuration (autotuner)
+    int ksplit = 1;               // K ranges run by separate CTAs (final tensor-core steps with few tiles)
 };
 
 // ---------------------------------------------------------------- cost model
@@ -141,6 +142,8 @@ struct Plan {
     void *d_ws = nullptr;
     void *d_zws = nullptr;
     double *d_zinfo = nullptr;             // [Z, scale]
+    void *d_kpart = nullptr;               // FP32 partials of K-split steps
+    int64_t kpart_bytes = 0;
     void *d_hostout = nullptr;             // buffer for tqc_contract_host
     int64_t d_hostout_bytes = 0;
     bool ready = false;
@@ -207,6 +210,10 @@ struct StepArgs {
     const void *A_lo = nullptr, *B_lo = nullptr;
     int32_t mb = 0, nb = 0, kb = 0;
     EpiParams epi;
+    // K split: split s of ksplit covers k-blocks [s kB / ksplit, (s+1) kB / ksplit)
+    // and stores its FP32 partial (EPI_F32) at epi.out + s * split_stride
+    int32_t ksplit = 1;
+    int64_t split_stride = 0;
 };
 
 struct IngestArgs {

@@ -49,7 +49,10 @@ enum Kind { K_BF16 = 0, K_BF16X3 = 1, K_TF32 = 2 };
 
 struct UmmaParams {
     int64_t n_tiles;
+    int64_t n_units;       // n_tiles * ksplit: unit u is split u / n_tiles of tile u % n_tiles
     int64_t col_tiles;
+    int64_t split_stride;  // elements between the FP32 partials of the splits
+    int32_t ksplit;        // K ranges per tile (deep form only)
     int32_t k_blocks;
     int32_t rowmajor;  // staging orientation (pick_staging)
     int32_t gmode;     // gather mode of the write-out (pick_staging)
@@ -261,9 +264,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 tma_load_2d(bsm, &tB, 0, 0, bfull);
                 if (KIND == K_BF16X3) tma_load_2d(bsm + C::B_BYTES, &tBl, 0, 0, bfull);
             }
-            for (int64_t tile = blockIdx.x; ok && tile < P.n_tiles; tile += gridDim.x) {
+            for (int64_t u = blockIdx.x; ok && u < P.n_units; u += gridDim.x) {
+                const int64_t sp = u / P.n_tiles, tile = u - sp * P.n_tiles;
                 const int rt = (int)(tile / P.col_tiles), ct = (int)(tile - (int64_t)rt * P.col_tiles);
-                for (int kb = 0; kb < P.k_blocks; ++kb, ++it) {
+                const int kb0 = (int)(sp * P.k_blocks / P.ksplit), kb1 = (int)((sp + 1) * P.k_blocks / P.ksplit);
+                for (int kb = kb0; kb < kb1; ++kb, ++it) {
                     const int s = (int)(it % nst);
                     const uint32_t ph = (uint32_t)((it / nst) & 1);
                     if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag)) {
@@ -307,7 +312,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 ok = mbar_wait(bfull, 0, abort_flag);
                 tc_fence_after();
             }
-            for (int64_t tile = blockIdx.x; ok && tile < P.n_tiles; tile += gridDim.x, ++lt) {
+            for (int64_t u = blockIdx.x; ok && u < P.n_units; u += gridDim.x, ++lt) {
+                const int64_t sp = u / P.n_tiles;
+                const int kb0 = (int)(sp * P.k_blocks / P.ksplit), kb1 = (int)((sp + 1) * P.k_blocks / P.ksplit);
                 const int acc = (int)(lt & 1);
                 const uint32_t aph = (uint32_t)((lt >> 1) & 1);
                 if (!mbar_wait(&tempty[acc], aph ^ 1u, abort_flag)) {
@@ -316,7 +323,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 }
                 tc_fence_after();
                 const uint32_t d = tmem_base + (uint32_t)(acc * BN);
-                for (int kb = 0; kb < P.k_blocks; ++kb, ++it) {
+                for (int kb = kb0; kb < kb1; ++kb, ++it) {
                     const int s = (int)(it % nst);
                     const uint32_t ph = (uint32_t)((it / nst) & 1);
                     if (!mbar_wait(&full[s], ph, abort_flag)) {
@@ -331,7 +338,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {  // four 32-byte K slices of the 128-byte atom
                         const uint64_t da = umma_desc(a0 + 32 * k), db = umma_desc(b0 + 32 * k);
-                        umma<KIND>(d, da, db, C::IDESC, (kb | k) != 0);
+                        umma<KIND>(d, da, db, C::IDESC, ((kb - kb0) | k) != 0);
                         if (KIND == K_BF16X3) {
                             umma<KIND>(d, da, umma_desc(bl + 32 * k), C::IDESC, 1u);
                             umma<KIND>(d, umma_desc(al + 32 * k), db, C::IDESC, 1u);
@@ -378,16 +385,19 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         // deposit adds to the chunk's: the bits are disjoint)
         const uint64_t off16 = pdep64(16, colmask);
         int64_t lt = 0;
-        for (int64_t tile = blockIdx.x; tile < P.n_tiles; tile += gridDim.x, ++lt) {
+        for (int64_t u = blockIdx.x; u < P.n_units; u += gridDim.x, ++lt) {
             const int acc = (int)(lt & 1);
             if (lane == 0) mbar_wait(&tfull[acc], (uint32_t)((lt >> 1) & 1), abort_flag);
             __syncwarp();
             if (*abort_flag) break;
             tc_fence_after();
+            const int64_t sp = u / P.n_tiles, tile = u - sp * P.n_tiles;
             const uint64_t rt = (uint64_t)(tile / P.col_tiles);
             const uint64_t ct = (uint64_t)(tile - (int64_t)rt * P.col_tiles);
-            // sub-tile column index ct * SUBS + h: the h bits are the lowest bits of highC (in coff)
-            const uint64_t base = warp_pdep64(rt, e.highR) | warp_pdep64(ct * SUBS, e.highC);
+            // sub-tile column index ct * SUBS + h: the h bits are the lowest bits of highC (in coff);
+            // split sp stores its partial sp * split_stride elements further on
+            const uint64_t base = (warp_pdep64(rt, e.highR) | warp_pdep64(ct * SUBS, e.highC)) +
+                                  (uint64_t)sp * (uint64_t)P.split_stride;
             // one half chunk (16 columns) at a time: 16 values in registers
             // keep the warp under its 96-register share without spills; the
             // accumulator is freed once the last half has been loaded
@@ -631,12 +641,19 @@ cudaError_t launch_kind(const StepArgs &a, int *d_err, cudaStream_t s) {
     p.col_tiles = a.nb >= lbn ? (int64_t)1 << (a.nb - lbn) : 1;
     p.n_tiles = row_tiles * p.col_tiles;
     p.k_blocks = (int)(K / C::BK);
+    // K split (deep form): every split needs at least one k-block, and its
+    // partial is stored as FP32
+    if (a.ksplit < 1 || a.ksplit > p.k_blocks || (a.ksplit > 1 && (!DEEP || a.epi.mode != EPI_F32)))
+        return cudaErrorInvalidValue;
+    p.ksplit = a.ksplit;
+    p.n_units = p.n_tiles * a.ksplit;
+    p.split_stride = a.ksplit > 1 ? a.split_stride : 0;
     p.bres = DEEP && p.k_blocks == 1 && p.col_tiles == 1;
     const StagePick pk = pick_staging(a.epi.lowRc, a.epi.lowCc);
     p.rowmajor = pk.rowmajor;
     p.gmode = pk.gmode;
     p.err = d_err;
-    const int64_t grid = std::min<int64_t>(p.n_tiles, sm_count());
+    const int64_t grid = std::min<int64_t>(p.n_units, sm_count());
     umma_step_kernel<BN, KIND, DEEP><<<(unsigned)grid, NTHREADS, C::SMEM, s>>>(tA, tB, tAl, tBl, p);
     return cudaGetLastError();
 }

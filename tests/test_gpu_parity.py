@@ -274,6 +274,31 @@ def test_tensor_core_deep_k_sliced_f64():
     check_fp32(got, want)
 
 
+# K split of the final step: a deep-K step with fewer tiles than SMs runs
+# its K loop in ranges on separate CTAs; the FP32 partials are summed in
+# FP64 and stored in the step's own output mode (scaled FP32 or FP64, or the
+# FP64 slice sum when sliced).
+KSPLIT_CASES = [  # (fa, fb, cuts, form); N = 2^8: 128 x 256 tiles in every precision
+    (8, 8, 6, "f32"), (8, 8, 7, "f32"), (9, 8, 7, "f64"), (8, 8, 7, "sliced"), (8, 9, 7, "sliced"),
+]
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "bf16", "tf32"])
+@pytest.mark.parametrize("fa,fb,cuts,form", KSPLIT_CASES)
+def test_final_step_k_split(prec, fa, fb, cuts, form):
+    net = two_node(1600 + fa * 7 + fb + cuts, fa, fb, cuts, True)
+    want = oracle.recon_bin(net)
+    kw = {"sliced": [2]} if form == "sliced" else {}
+    got, z, d = run(net, out_f64=form != "f32", precision=prec, **kw)
+    st = d["steps"][-1]
+    assert st["tile"] == UMMA_128x256_DEEP and st["ksplit"] > 1, st
+    assert d["sliced"] == ([2] if form == "sliced" else [])
+    if prec == "bf16x3":
+        check_fp32(got, want)
+    else:
+        check_tc(prec, got, net, d, want)
+
+
 def kron_final_network(seed, cuts, fb=8):
     """Two nodes whose final step writes the bin in qubit order with a
     column qubit at bit 0 and seven row qubits above it: the direct
