@@ -135,7 +135,10 @@ typedef struct {
     int32_t precision;                   /* TQC_PREC_* */
     int32_t planner;                     /* TQC_PLANNER_* */
     uint64_t mem_budget_bytes;           /* device bytes for operands, intermediates and the
-                                            FP64 slice sum; 0 = unlimited */
+                                            FP64 slice sum; 0 = unlimited.  A final step split
+                                            along K (few tiles, long K loop) also keeps FP32
+                                            partials of at most budget / 16 bytes (1 GiB when
+                                            unlimited) */
     const char *costmodel_path;          /* learned cost model file (TQC_PLANNER_LEARNED) */
     int32_t autotune;                    /* 1 = time candidate tiles on first contract */
     int32_t n_order;                     /* optional forced contraction order: n_order pairs */
@@ -175,7 +178,11 @@ TQC_API tqc_status tqc_plan_step(tqc_plan_t plan, int32_t step, int32_t *log2_m,
 
 /*
  * Plan summary as JSON in buf (NUL-terminated, truncated to size).  Returns
- * the full length needed, excluding the NUL, or -1 on a bad handle.
+ * the full length needed, excluding the NUL, or -1 on a bad handle.  Each
+ * step lists its shape, class, precision, result layout, tile configuration
+ * and "ksplit" (K ranges run by separate CTAs, 1 = none).  The first
+ * contract sets tiles and splits (0 and 1 before it); the autotuner may
+ * change them.
  */
 TQC_API int32_t tqc_plan_describe(tqc_plan_t plan, char *buf, int32_t size);
 
