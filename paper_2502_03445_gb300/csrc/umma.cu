@@ -14,15 +14,20 @@
 //   warp 1      allocates TMEM (two FP32 accumulators of 128 x BN) and issues
 //               tcgen05.mma from one thread; tcgen05.commit frees stages and
 //               hands accumulators to the epilogue
-//   warps 2..17 epilogue: tcgen05.ld 32 columns at a time, stage the tile in
-//               shared memory in the orientation that makes the result's
-//               lowest bits contiguous, then write 16-byte runs to HBM
-// The deep-K form (K of thousands, few output tiles) drops the staging
-// buffers: every epilogue warp loads its 32 x 32 block from TMEM, frees the
-// accumulator and stores straight to HBM, which the next tile's long K loop
-// hides; the freed shared memory deepens the operand ring (192 KB in
-// flight) and allows 128 x 256 MMA tiles, since that loop is bound by the
-// latency of the copies, not by the tensor pipe.
+//   warps 2..17 epilogue (staged form): tcgen05.ld 32 columns at a time,
+//               stage the tile in shared memory in the orientation that
+//               makes the result's lowest bits contiguous, then write
+//               16-byte runs to HBM
+// The direct form (deep-K steps, and layouts whose warp stores fill whole
+// sectors) drops the staging buffers: every epilogue warp loads its 32-row
+// block from TMEM 16 columns at a time, frees the accumulator and stores
+// straight to HBM, which the next tile's K loop hides; the freed shared
+// memory deepens the operand ring (192 KB in flight) and allows 128 x 256
+// MMA tiles.  A step with one k-block and one column tile keeps B resident.
+// In the direct form a tile's K loop may be split into ranges run as
+// separate units (split s of every tile after split s - 1), each storing an
+// FP32 partial that a reduce pass sums: this evens the waves of a step with
+// few tiles.
 // Every wait is bounded (clock64); a wait that gives up sets an error word,
 // drains the copies and MMAs it issued, frees TMEM and returns.
 #include <cuda.h>
