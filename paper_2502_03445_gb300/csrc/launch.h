@@ -45,6 +45,10 @@ int exec_epi_mode(int storage);
 // Tile configuration of a step when it is not autotuned (out_esize: bytes
 // per result element its epilogue writes).
 constexpr int DEEP_MIN_LOG2_K = 12;
+// Direct-form steps from this K on (rows up to 64 KB) use 64-byte k-blocks:
+// measured 6% faster at K = 2^14, slower at K = 2^10 (short loops) and at
+// K = 2^18 (rows of 512 KB: twice the boxes per byte, each across pages).
+constexpr int SW64_MIN_LOG2_K = 12;
 int default_step_tile(const StepPlan &st, int out_esize);
 // K splits of a final tensor-core step with too few tiles to fill the GPU
 // evenly (1 = no split); max_part_bytes caps the FP32 partials it stores.

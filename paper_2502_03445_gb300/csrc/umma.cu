@@ -58,6 +58,7 @@ struct UmmaParams {
     int64_t col_tiles;
     int64_t split_stride;  // elements between the FP32 partials of the splits
     int32_t ksplit;        // K ranges per tile (deep form only)
+    int32_t sw64;          // deep form: 64-byte swizzled k-blocks (half the K per stage, twice the stages)
     int32_t k_blocks;
     int32_t rowmajor;  // staging orientation (pick_staging)
     int32_t gmode;     // gather mode of the write-out (pick_staging)
@@ -135,14 +136,16 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, i
         : "memory");
 }
 
-// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row atoms
-// 1024 bytes apart (stride byte offset), leading byte offset unused.
-__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr) {
+// Shared-memory matrix descriptor: K-major, rows of rowb bytes (128 or 64)
+// swizzled over their whole span, 8-row atoms 8 * rowb bytes apart (stride
+// byte offset), leading byte offset unused; layout type 2 = 128-byte
+// swizzle, 4 = 64-byte swizzle.
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, int rowb) {
     uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
     d |= (uint64_t)1 << 16;
-    d |= (uint64_t)(1024 >> 4) << 32;
+    d |= (uint64_t)((8 * rowb) >> 4) << 32;
     d |= (uint64_t)1 << 46;
-    d |= (uint64_t)2 << 61;
+    d |= (uint64_t)(rowb == 128 ? 2 : 4) << 61;
     return d;
 }
 
@@ -222,10 +225,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     // With B resident (deep form, a single k-block and column tile: B is the
     // same for every tile) the ring holds A only and B sits at its end.
     const bool bres = DEEP && P.bres;
-    const int sbytes = bres ? C::PLANES * C::A_BYTES : C::STAGE_BYTES;
-    const int nfit = (C::RING - C::PLANES * C::B_BYTES) / sbytes;
-    const int nst = bres ? (nfit < C::MAXST ? nfit : (int)C::MAXST) : (int)C::STAGES;
-    uint8_t *bsm = stages + C::RING - C::PLANES * C::B_BYTES;
+    // bytes of K per operand row in one k-block (the swizzle span), and the
+    // plane sizes of a stage
+    const int rowb = (DEEP && P.sw64) ? 64 : 128;
+    const int bk = rowb / C::ELEM, ksl = rowb / 32;  // elements of K per k-block; 32-byte MMA slices
+    const int ab = BM * rowb, bb = BN * rowb;
+    const int sbytes = bres ? C::PLANES * ab : C::PLANES * (ab + bb);
+    const int nfit = (C::RING - (bres ? C::PLANES * bb : 0)) / sbytes;
+    const int nst = nfit < C::MAXST ? nfit : (int)C::MAXST;
+    uint8_t *bsm = stages + C::RING - C::PLANES * bb;
     volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
     uint64_t *tile_base_slot = (uint64_t *)(tmem_slot + 2);  // epilogue: base offsets of two sub-tiles
     uint8_t *tb_pos = (uint8_t *)(tile_base_slot + 2);       // epilogue: tile-index bit positions
@@ -265,9 +273,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             int64_t it = 0;
             bool ok = true;
             if (bres) {  // the one B tile, loaded once
-                mbar_expect_tx(bfull, C::PLANES * C::B_BYTES);
+                mbar_expect_tx(bfull, C::PLANES * bb);
                 tma_load_2d(bsm, &tB, 0, 0, bfull);
-                if (KIND == K_BF16X3) tma_load_2d(bsm + C::B_BYTES, &tBl, 0, 0, bfull);
+                if (KIND == K_BF16X3) tma_load_2d(bsm + bb, &tBl, 0, 0, bfull);
             }
             for (int64_t u = blockIdx.x; ok && u < P.n_units; u += gridDim.x) {
                 const int64_t sp = u / P.n_tiles, tile = u - sp * P.n_tiles;
@@ -282,14 +290,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     }
                     uint8_t *sa = stages + s * sbytes;
                     mbar_expect_tx(&full[s], (uint32_t)sbytes);
-                    tma_load_2d(sa, &tA, kb * C::BK, rt * BM, &full[s]);
+                    tma_load_2d(sa, &tA, kb * bk, rt * BM, &full[s]);
                     if (bres) {
-                        if (KIND == K_BF16X3) tma_load_2d(sa + C::A_BYTES, &tAl, kb * C::BK, rt * BM, &full[s]);
+                        if (KIND == K_BF16X3) tma_load_2d(sa + ab, &tAl, kb * bk, rt * BM, &full[s]);
                     } else {
-                        tma_load_2d(sa + C::A_BYTES, &tB, kb * C::BK, ct * BN, &full[s]);
+                        tma_load_2d(sa + ab, &tB, kb * bk, ct * BN, &full[s]);
                         if (KIND == K_BF16X3) {
-                            tma_load_2d(sa + C::A_BYTES + C::B_BYTES, &tAl, kb * C::BK, rt * BM, &full[s]);
-                            tma_load_2d(sa + 2 * C::A_BYTES + C::B_BYTES, &tBl, kb * C::BK, ct * BN, &full[s]);
+                            tma_load_2d(sa + ab + bb, &tAl, kb * bk, rt * BM, &full[s]);
+                            tma_load_2d(sa + 2 * ab + bb, &tBl, kb * bk, ct * BN, &full[s]);
                         }
                     }
                 }
@@ -337,16 +345,18 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     }
                     tc_fence_after();
                     const uint32_t a0 = smem_u32(stages + s * sbytes);
-                    const uint32_t b0 = bres ? smem_u32(bsm) : a0 + C::A_BYTES;
-                    const uint32_t al = bres ? a0 + C::A_BYTES : b0 + C::B_BYTES;
-                    const uint32_t bl = bres ? b0 + C::B_BYTES : al + C::A_BYTES;
+                    const uint32_t b0 = bres ? smem_u32(bsm) : a0 + ab;
+                    const uint32_t al = bres ? a0 + ab : b0 + bb;
+                    const uint32_t bl = bres ? b0 + bb : al + ab;
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) {  // four 32-byte K slices of the 128-byte atom
-                        const uint64_t da = umma_desc(a0 + 32 * k), db = umma_desc(b0 + 32 * k);
-                        umma<KIND>(d, da, db, C::IDESC, ((kb - kb0) | k) != 0);
-                        if (KIND == K_BF16X3) {
-                            umma<KIND>(d, da, umma_desc(bl + 32 * k), C::IDESC, 1u);
-                            umma<KIND>(d, umma_desc(al + 32 * k), db, C::IDESC, 1u);
+                    for (int k = 0; k < 4; ++k) {  // 32-byte K slices of the swizzled row: 4 (128 B) or 2 (64 B)
+                        if (k < ksl) {
+                            const uint64_t da = umma_desc(a0 + 32 * k, rowb), db = umma_desc(b0 + 32 * k, rowb);
+                            umma<KIND>(d, da, db, C::IDESC, ((kb - kb0) | k) != 0);
+                            if (KIND == K_BF16X3) {
+                                umma<KIND>(d, da, umma_desc(bl + 32 * k, rowb), C::IDESC, 1u);
+                                umma<KIND>(d, umma_desc(al + 32 * k, rowb), db, C::IDESC, 1u);
+                            }
                         }
                     }
                     umma_commit(&empty[s]);
@@ -596,9 +606,12 @@ cudaError_t get_encode() {
     return g_encode ? cudaSuccess : cudaErrorNotSupported;
 }
 
-// 2-D K-major operand: `rows` rows of `k` elements, box = (BK elements, box_rows)
+// 2-D K-major operand: `rows` rows of `k` elements, box = (bk elements,
+// box_rows), bk * elem bytes (128 or 64) swizzled over that span
 cudaError_t encode(CUtensorMap *m, const void *ptr, int elem, uint64_t k, uint64_t rows, uint32_t bk,
                    uint32_t box_rows) {
+    const uint32_t span = bk * (uint32_t)elem;
+    if (span != 128 && span != 64) return cudaErrorInvalidValue;
     if (!ptr || ((uintptr_t)ptr & 15) || rows > (1ull << 32)) return cudaErrorInvalidValue;
     cuuint64_t dims[2] = {k, rows};
     cuuint64_t strides[1] = {k * (uint64_t)elem};
@@ -606,7 +619,8 @@ cudaError_t encode(CUtensorMap *m, const void *ptr, int elem, uint64_t k, uint64
     cuuint32_t estr[2] = {1, 1};
     CUresult r = g_encode(m, elem == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
                           const_cast<void *>(ptr), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                          CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          span == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
@@ -627,13 +641,19 @@ cudaError_t launch_kind(const StepArgs &a, int *d_err, cudaStream_t s) {
         attr = true;
     }
     const uint64_t M = 1ull << a.mb, N = 1ull << a.nb, K = 1ull << a.kb;
-    if (K < (uint64_t)C::BK) return cudaErrorInvalidValue;
+    // Long K loops take 64-byte k-blocks: stages of half the bytes, so twice
+    // as many copies are in flight ahead of the tensor pipe.  Not for rows
+    // longer than 64 KB: a box then spans many pages, and twice the boxes
+    // per byte cost more in address translation than the deeper ring gains.
+    const bool sw64 = DEEP && K >= ((uint64_t)1 << SW64_MIN_LOG2_K) && K * C::ELEM <= ((uint64_t)1 << 16);
+    const uint32_t bk = (sw64 ? 64 : 128) / C::ELEM;
+    if (K < (uint64_t)bk) return cudaErrorInvalidValue;
     CUtensorMap tA, tB, tAl, tBl;
-    if ((e = encode(&tA, a.A, C::ELEM, K, M, C::BK, BM)) != cudaSuccess) return e;
-    if ((e = encode(&tB, a.B, C::ELEM, K, N, C::BK, BN)) != cudaSuccess) return e;
+    if ((e = encode(&tA, a.A, C::ELEM, K, M, bk, BM)) != cudaSuccess) return e;
+    if ((e = encode(&tB, a.B, C::ELEM, K, N, bk, BN)) != cudaSuccess) return e;
     if (KIND == K_BF16X3) {
-        if ((e = encode(&tAl, a.A_lo, C::ELEM, K, M, C::BK, BM)) != cudaSuccess) return e;
-        if ((e = encode(&tBl, a.B_lo, C::ELEM, K, N, C::BK, BN)) != cudaSuccess) return e;
+        if ((e = encode(&tAl, a.A_lo, C::ELEM, K, M, bk, BM)) != cudaSuccess) return e;
+        if ((e = encode(&tBl, a.B_lo, C::ELEM, K, N, bk, BN)) != cudaSuccess) return e;
     } else {
         tAl = tA;
         tBl = tB;
@@ -645,7 +665,8 @@ cudaError_t launch_kind(const StepArgs &a, int *d_err, cudaStream_t s) {
     const int64_t row_tiles = (int64_t)1 << (a.mb - a.epi.a_bits);
     p.col_tiles = a.nb >= lbn ? (int64_t)1 << (a.nb - lbn) : 1;
     p.n_tiles = row_tiles * p.col_tiles;
-    p.k_blocks = (int)(K / C::BK);
+    p.k_blocks = (int)(K / bk);
+    p.sw64 = sw64;
     // K split (deep form): every split needs at least one k-block, and its
     // partial is stored as FP32
     if (a.ksplit < 1 || a.ksplit > p.k_blocks || (a.ksplit > 1 && (!DEEP || a.epi.mode != EPI_F32)))
