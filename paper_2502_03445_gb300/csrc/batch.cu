@@ -116,6 +116,20 @@ __device__ __forceinline__ void btma_load(void *dst, const CUtensorMap *map, int
         "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(s_u32(bar))
         : "memory");
 }
+__device__ __forceinline__ void btma_load3(void *dst, const CUtensorMap *map, int c0, int c1, int c2, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::
+            "r"(s_u32(dst)),
+        "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(c2), "r"(s_u32(bar))
+        : "memory");
+}
+// One k-block of an operand from element kel of K and row `row`; K-blocked
+// operands ([K / 64][rows][64]) are addressed as (kel mod 64, row, kel / 64).
+__device__ __forceinline__ void btma_op(void *dst, const CUtensorMap *map, int kel, int row, uint64_t *bar,
+                                        bool kblk) {
+    if (kblk) btma_load3(dst, map, kel & 63, row, kel >> 6, bar);
+    else btma_load(dst, map, kel, row, bar);
+}
 __device__ __forceinline__ void bcommit(uint64_t *bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(s_u32(bar))
                  : "memory");
@@ -400,14 +414,15 @@ __global__ void __launch_bounds__(BT, 1)
             const int nst = nfit < MAXST ? nfit : MAXST;
             uint8_t *bsm = ring + RING - planes * b_bytes;
             const int bk = st.prec == TQC_PREC_TF32 ? 32 : 64;
+            const bool kblk = st.a.kblk != 0;
             const int64_t t_end = item.tile + item.count;
             if (warp == 0) {
                 // ---------------------------------------- TMA producer
                 if (lane == 0) {
                     if (st.bres) {
                         bmbar_expect_tx(&ctl->bfull, (uint32_t)(planes * b_bytes));
-                        btma_load(bsm, &st.maps[1], 0, 0, &ctl->bfull);
-                        if (x3) btma_load(bsm + b_bytes, &st.maps[3], 0, 0, &ctl->bfull);
+                        btma_op(bsm, &st.maps[1], 0, 0, &ctl->bfull, kblk);
+                        if (x3) btma_op(bsm + b_bytes, &st.maps[3], 0, 0, &ctl->bfull, kblk);
                     }
                     int s = 0;
                     for (int64_t tile = item.tile; tile < t_end && !*abort_flag; ++tile) {
@@ -420,14 +435,15 @@ __global__ void __launch_bounds__(BT, 1)
                             used |= 1u << s;
                             uint8_t *sa = ring + s * sbytes;
                             bmbar_expect_tx(&ctl->full[s], (uint32_t)sbytes);
-                            btma_load(sa, &st.maps[0], kb * bk, rt * BM, &ctl->full[s]);
+                            btma_op(sa, &st.maps[0], kb * bk, rt * BM, &ctl->full[s], kblk);
                             if (st.bres) {
-                                if (x3) btma_load(sa + a_bytes, &st.maps[2], kb * bk, rt * BM, &ctl->full[s]);
+                                if (x3) btma_op(sa + a_bytes, &st.maps[2], kb * bk, rt * BM, &ctl->full[s], kblk);
                             } else {
-                                btma_load(sa + a_bytes, &st.maps[1], kb * bk, ct * st.bn, &ctl->full[s]);
+                                btma_op(sa + a_bytes, &st.maps[1], kb * bk, ct * st.bn, &ctl->full[s], kblk);
                                 if (x3) {
-                                    btma_load(sa + a_bytes + b_bytes, &st.maps[2], kb * bk, rt * BM, &ctl->full[s]);
-                                    btma_load(sa + 2 * a_bytes + b_bytes, &st.maps[3], kb * bk, ct * st.bn, &ctl->full[s]);
+                                    btma_op(sa + a_bytes + b_bytes, &st.maps[2], kb * bk, rt * BM, &ctl->full[s], kblk);
+                                    btma_op(sa + 2 * a_bytes + b_bytes, &st.maps[3], kb * bk, ct * st.bn, &ctl->full[s],
+                                            kblk);
                                 }
                             }
                             s = s + 1 == nst ? 0 : s + 1;

@@ -101,6 +101,7 @@ StepArgs step_args(const Plan &p, const std::vector<TensorPlan> &T, const StepPl
     a.mb = st.mb;
     a.nb = st.nb;
     a.kb = st.kb;
+    a.kblk = st.kblk ? 1 : 0;
     a.epi = make_epi(st.maskR, st.maskC, st.mb, st.nb, tile);
     (void)p;
     return a;

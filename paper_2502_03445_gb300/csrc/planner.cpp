@@ -417,6 +417,13 @@ void assign_layouts(Built &B, int m) {
         }
         std::vector<int> shared_sorted = shared;  // membership tests
         std::sort(shared_sorted.begin(), shared_sorted.end());
+        // Tensor-core operands whose rows exceed 64 KB are K-blocked: the
+        // lowest three shared cuts (64 elements) stay lowest, the row bits
+        // follow, then the rest of K.  A 128-row copy box is then one
+        // contiguous region instead of 128 rows strided across many pages.
+        const int elem = st.prec == TQC_PREC_TF32 ? 4 : 2;
+        st.kblk = st.klass == KC_UMMA && st.kb >= 6 && ((int64_t)elem << st.kb) > ((int64_t)1 << 16);
+        const size_t n_low = st.kblk ? 3 : shared.size();
         auto make = [&](TensorPlan &T, uint64_t *mask) {
             std::vector<std::pair<int, Mode>> outer;  // (position in LC, mode)
             for (int q : T.qubits) {
@@ -430,12 +437,13 @@ void assign_layouts(Built &B, int m) {
                 }
             std::sort(outer.begin(), outer.end(), [](auto &x, auto &y) { return x.first < y.first; });
             T.layout.modes.clear();
-            for (int c : shared) T.layout.modes.push_back({1, (int16_t)c});
+            for (size_t i = 0; i < n_low; ++i) T.layout.modes.push_back({1, (int16_t)shared[i]});
             uint64_t mk = 0;
             for (auto &pm : outer) {
                 T.layout.modes.push_back(pm.second);
                 for (int b = 0; b < pm.second.bits(); ++b) mk |= 1ull << (pm.first + b);
             }
+            for (size_t i = n_low; i < shared.size(); ++i) T.layout.modes.push_back({1, (int16_t)shared[i]});
             *mask = mk;
         };
         make(A, &st.maskR);
@@ -824,7 +832,7 @@ std::string plan_describe(const Plan &pl) {
            << (st.klass == KC_UMMA ? "tcgen05" : "simt") << "\",\"prec\":\""
            << (st.klass == KC_UMMA ? prec_name(st.prec) : "fp32") << "\",\"out_layout\":" << mode_str(p->tensors[st.c].layout)
            << ",\"mask_r\":" << st.maskR << ",\"mask_c\":" << st.maskC << ",\"tile\":" << st.tile
-           << ",\"ksplit\":" << st.ksplit << "}";
+           << ",\"ksplit\":" << st.ksplit << ",\"kblk\":" << (st.kblk ? 1 : 0) << "}";
     }
     os << "],\"layouts\":[";
     for (size_t i = 0; i < p->tensors.size(); ++i) os << (i ? "," : "") << mode_str(p->tensors[i].layout);

@@ -100,6 +100,7 @@ struct StepPlan {
     bool final = false;
     int tile = 0;                 // tile configuration (autotuner)
     int ksplit = 1;               // K ranges run by separate CTAs (final tensor-core steps with few tiles)
+    bool kblk = false;            // operands stored K-blocked: [K / 64][rows][64] (tensor-core steps with long rows)
 };
 
 // ---------------------------------------------------------------- cost model
@@ -214,6 +215,8 @@ struct StepArgs {
     // and stores its FP32 partial (EPI_F32) at epi.out + s * split_stride
     int32_t ksplit = 1;
     int64_t split_stride = 0;
+    // operands K-blocked: element (r, k) at (k / 64) * rows * 64 + r * 64 + k % 64
+    int32_t kblk = 0;
 };
 
 struct IngestArgs {

@@ -59,6 +59,7 @@ struct UmmaParams {
     int64_t split_stride;  // elements between the FP32 partials of the splits
     int32_t ksplit;        // K ranges per tile (deep form only)
     int32_t sw64;          // deep form: 64-byte swizzled k-blocks (half the K per stage, twice the stages)
+    int32_t kblk;          // operands K-blocked ([K / 64][rows][64]): 3-D copies
     int32_t k_blocks;
     int32_t rowmajor;  // staging orientation (pick_staging)
     int32_t gmode;     // gather mode of the write-out (pick_staging)
@@ -134,6 +135,23 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, i
             smem_u32(dst)),
         "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(smem_u32(bar))
         : "memory");
+}
+
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int c0, int c1, int c2,
+                                            uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::
+            "r"(smem_u32(dst)),
+        "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// One k-block of an operand: K elements from kel on, rows from row on.  A
+// K-blocked operand is addressed as (kel mod 64, row, kel / 64).
+__device__ __forceinline__ void tma_load_op(void *dst, const CUtensorMap *map, int kel, int row, uint64_t *bar,
+                                            bool kblk) {
+    if (kblk) tma_load_3d(dst, map, kel & 63, row, kel >> 6, bar);
+    else tma_load_2d(dst, map, kel, row, bar);
 }
 
 // Shared-memory matrix descriptor: K-major, rows of rowb bytes (128 or 64)
@@ -228,6 +246,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     // bytes of K per operand row in one k-block (the swizzle span), and the
     // plane sizes of a stage
     const int rowb = (DEEP && P.sw64) ? 64 : 128;
+    const bool kblk = P.kblk != 0;
     const int bk = rowb / C::ELEM, ksl = rowb / 32;  // elements of K per k-block; 32-byte MMA slices
     const int ab = BM * rowb, bb = BN * rowb;
     const int sbytes = bres ? C::PLANES * ab : C::PLANES * (ab + bb);
@@ -274,8 +293,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             bool ok = true;
             if (bres) {  // the one B tile, loaded once
                 mbar_expect_tx(bfull, C::PLANES * bb);
-                tma_load_2d(bsm, &tB, 0, 0, bfull);
-                if (KIND == K_BF16X3) tma_load_2d(bsm + bb, &tBl, 0, 0, bfull);
+                tma_load_op(bsm, &tB, 0, 0, bfull, kblk);
+                if (KIND == K_BF16X3) tma_load_op(bsm + bb, &tBl, 0, 0, bfull, kblk);
             }
             for (int64_t u = blockIdx.x; ok && u < P.n_units; u += gridDim.x) {
                 const int64_t sp = u / P.n_tiles, tile = u - sp * P.n_tiles;
@@ -290,14 +309,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     }
                     uint8_t *sa = stages + s * sbytes;
                     mbar_expect_tx(&full[s], (uint32_t)sbytes);
-                    tma_load_2d(sa, &tA, kb * bk, rt * BM, &full[s]);
+                    tma_load_op(sa, &tA, kb * bk, rt * BM, &full[s], kblk);
                     if (bres) {
-                        if (KIND == K_BF16X3) tma_load_2d(sa + ab, &tAl, kb * bk, rt * BM, &full[s]);
+                        if (KIND == K_BF16X3) tma_load_op(sa + ab, &tAl, kb * bk, rt * BM, &full[s], kblk);
                     } else {
-                        tma_load_2d(sa + ab, &tB, kb * bk, ct * BN, &full[s]);
+                        tma_load_op(sa + ab, &tB, kb * bk, ct * BN, &full[s], kblk);
                         if (KIND == K_BF16X3) {
-                            tma_load_2d(sa + ab + bb, &tAl, kb * bk, rt * BM, &full[s]);
-                            tma_load_2d(sa + 2 * ab + bb, &tBl, kb * bk, ct * BN, &full[s]);
+                            tma_load_op(sa + ab + bb, &tAl, kb * bk, rt * BM, &full[s], kblk);
+                            tma_load_op(sa + 2 * ab + bb, &tBl, kb * bk, ct * BN, &full[s], kblk);
                         }
                     }
                 }
@@ -606,19 +625,28 @@ cudaError_t get_encode() {
     return g_encode ? cudaSuccess : cudaErrorNotSupported;
 }
 
-// 2-D K-major operand: `rows` rows of `k` elements, box = (bk elements,
-// box_rows), bk * elem bytes (128 or 64) swizzled over that span
+// K-major operand of `rows` rows of `k` elements, box = (bk elements,
+// box_rows), bk * elem bytes (128 or 64) swizzled over that span.  Row-major
+// operands are 2-D (k, rows); K-blocked ones ([k / 64][rows][64]) are 3-D
+// (64, rows, k / 64) with a box one block deep.
 cudaError_t encode(CUtensorMap *m, const void *ptr, int elem, uint64_t k, uint64_t rows, uint32_t bk,
-                   uint32_t box_rows) {
+                   uint32_t box_rows, bool kblk = false) {
     const uint32_t span = bk * (uint32_t)elem;
     if (span != 128 && span != 64) return cudaErrorInvalidValue;
     if (!ptr || ((uintptr_t)ptr & 15) || rows > (1ull << 32)) return cudaErrorInvalidValue;
-    cuuint64_t dims[2] = {k, rows};
-    cuuint64_t strides[1] = {k * (uint64_t)elem};
-    cuuint32_t box[2] = {bk, box_rows};
-    cuuint32_t estr[2] = {1, 1};
-    CUresult r = g_encode(m, elem == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
-                          const_cast<void *>(ptr), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+    if (kblk && (k % 64 != 0 || bk > 64)) return cudaErrorInvalidValue;
+    cuuint64_t dims[3] = {k, rows, 1};
+    cuuint64_t strides[2] = {k * (uint64_t)elem, 0};
+    cuuint32_t box[3] = {bk, box_rows, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    if (kblk) {
+        dims[0] = 64;
+        dims[2] = k / 64;
+        strides[0] = 64 * (uint64_t)elem;
+        strides[1] = rows * 64 * (uint64_t)elem;
+    }
+    CUresult r = g_encode(m, elem == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
+                          kblk ? 3 : 2, const_cast<void *>(ptr), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                           span == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -645,15 +673,16 @@ cudaError_t launch_kind(const StepArgs &a, int *d_err, cudaStream_t s) {
     // as many copies are in flight ahead of the tensor pipe.  Not for rows
     // longer than 64 KB: a box then spans many pages, and twice the boxes
     // per byte cost more in address translation than the deeper ring gains.
-    const bool sw64 = DEEP && K >= ((uint64_t)1 << SW64_MIN_LOG2_K) && K * C::ELEM <= ((uint64_t)1 << 16);
+    const bool sw64 = DEEP && !a.kblk && K >= ((uint64_t)1 << SW64_MIN_LOG2_K) && K * C::ELEM <= ((uint64_t)1 << 16);
     const uint32_t bk = (sw64 ? 64 : 128) / C::ELEM;
     if (K < (uint64_t)bk) return cudaErrorInvalidValue;
     CUtensorMap tA, tB, tAl, tBl;
-    if ((e = encode(&tA, a.A, C::ELEM, K, M, bk, BM)) != cudaSuccess) return e;
-    if ((e = encode(&tB, a.B, C::ELEM, K, N, bk, BN)) != cudaSuccess) return e;
+    const bool kb3 = a.kblk != 0;
+    if ((e = encode(&tA, a.A, C::ELEM, K, M, bk, BM, kb3)) != cudaSuccess) return e;
+    if ((e = encode(&tB, a.B, C::ELEM, K, N, bk, BN, kb3)) != cudaSuccess) return e;
     if (KIND == K_BF16X3) {
-        if ((e = encode(&tAl, a.A_lo, C::ELEM, K, M, bk, BM)) != cudaSuccess) return e;
-        if ((e = encode(&tBl, a.B_lo, C::ELEM, K, N, bk, BN)) != cudaSuccess) return e;
+        if ((e = encode(&tAl, a.A_lo, C::ELEM, K, M, bk, BM, kb3)) != cudaSuccess) return e;
+        if ((e = encode(&tBl, a.B_lo, C::ELEM, K, N, bk, BN, kb3)) != cudaSuccess) return e;
     } else {
         tAl = tA;
         tBl = tB;
@@ -667,6 +696,7 @@ cudaError_t launch_kind(const StepArgs &a, int *d_err, cudaStream_t s) {
     p.n_tiles = row_tiles * p.col_tiles;
     p.k_blocks = (int)(K / bk);
     p.sw64 = sw64;
+    p.kblk = kb3;
     // K split (deep form): every split needs at least one k-block, and its
     // partial is stored as FP32
     if (a.ksplit < 1 || a.ksplit > p.k_blocks || (a.ksplit > 1 && (!DEEP || a.epi.mode != EPI_F32)))
@@ -706,11 +736,12 @@ cudaError_t umma_make_maps(int prec, const StepArgs &a, int bn, void *maps_out) 
     const uint32_t bk = 128 / elem;
     const uint64_t M = 1ull << a.mb, N = 1ull << a.nb, K = 1ull << a.kb;
     if (K < bk) return cudaErrorInvalidValue;
-    if ((e = encode(&m[0], a.A, elem, K, M, bk, BM)) != cudaSuccess) return e;
-    if ((e = encode(&m[1], a.B, elem, K, N, bk, (uint32_t)bn)) != cudaSuccess) return e;
+    const bool kb3 = a.kblk != 0;
+    if ((e = encode(&m[0], a.A, elem, K, M, bk, BM, kb3)) != cudaSuccess) return e;
+    if ((e = encode(&m[1], a.B, elem, K, N, bk, (uint32_t)bn, kb3)) != cudaSuccess) return e;
     if (prec == TQC_PREC_BF16X3) {
-        if ((e = encode(&m[2], a.A_lo, elem, K, M, bk, BM)) != cudaSuccess) return e;
-        if ((e = encode(&m[3], a.B_lo, elem, K, N, bk, (uint32_t)bn)) != cudaSuccess) return e;
+        if ((e = encode(&m[2], a.A_lo, elem, K, M, bk, BM, kb3)) != cudaSuccess) return e;
+        if ((e = encode(&m[3], a.B_lo, elem, K, N, bk, (uint32_t)bn, kb3)) != cudaSuccess) return e;
     } else {
         m[2] = m[0];
         m[3] = m[1];

@@ -63,6 +63,21 @@ def test_batch_matches_oracle(mode):
         p.close()
 
 
+def test_batch_k_blocked_operands():
+    """Plans whose deep steps read K-blocked operands (rows over 64 KB)."""
+    nets = [tensors.pseudo_physical_network(14, [(0, 1)] * 8, [list(range(7)), list(range(7, 14))], 3200),
+            tensors.pseudo_physical_network(15, [(0, 1)] * 8, [list(range(8)), list(range(8, 15))], 3201)]
+    precs = ["bf16x3", "tf32"]
+    hs, plans, outs_, want = prepared(nets, precs)
+    for p in plans:
+        assert any(st["kblk"] for st in p.describe()["steps"])
+    tqc.contract_batch(plans, outs_)
+    tqc.batch_status()
+    check(outs_, want, 2e-3)
+    for p in plans:
+        p.close()
+
+
 def test_batch_under_cuda_graph():
     nets = uneven_networks()
     hs, plans, outs, want = prepared(nets, ["auto"] * len(nets))

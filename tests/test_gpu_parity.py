@@ -7,6 +7,8 @@ All sizes are powers of two (dimension 2 outputs, dimension 4 cuts), so the
 "ragged" cases are tiles wider than the operand (M, N or K below the tile),
 odd qubit counts per subcircuit, a single state (F = 0), a single subcircuit,
 zero cuts, and slicing."""
+import functools
+
 import numpy as np
 import pytest
 
@@ -295,6 +297,56 @@ def test_final_step_k_split(prec, fa, fb, cuts, form):
     assert d["sliced"] == ([2] if form == "sliced" else [])
     if prec == "bf16x3":
         check_fp32(got, want)
+    else:
+        check_tc(prec, got, net, d, want)
+
+
+# K-blocked operands: tensor-core operands with rows longer than 64 KB are
+# stored as [K / 64][rows][64] and copied with 3-D boxes.  Leaves get the
+# layout from the ingest, an intermediate from its producing step.
+def kblk_three_node(seed):
+    outs = [list(range(0, 8)), list(range(8, 12)), list(range(12, 15))]
+    return tensors.pseudo_physical_network(15, [(0, 1)] * 8 + [(1, 2)], outs, seed)
+
+
+@functools.lru_cache(maxsize=2)
+def kblk_three_node_oracle(seed):
+    return oracle.recon_bin(kblk_three_node(seed))
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "bf16", "tf32"])
+def test_k_blocked_operands(prec):
+    """M = N = 128: the direct 128 x 128 form with a K split (split BF16)
+    and the staged 128 x 128 form (BF16, TF32)."""
+    net = two_node(1700, 7, 7, 8, True)
+    want = oracle.recon_bin(net)
+    got, z, d = run(net, precision=prec)
+    st = d["steps"][-1]
+    assert st["class"] == "tcgen05" and st["log2_k"] == 16 and st["kblk"] == 1, st
+    if prec == "bf16x3":
+        check_fp32(got, want)
+    else:
+        check_tc(prec, got, net, d, want)
+
+
+@pytest.mark.parametrize("order", [[[1, 2], [0, 3]], [[0, 1], [3, 2]]])
+@pytest.mark.parametrize("prec", ["bf16x3", "tf32"])
+def test_k_blocked_intermediate_and_leaves(order, prec):
+    """Order 1: a CUDA-core step writes the K-blocked operand of a deep
+    tensor-core final step.  Order 2: the ingest writes K-blocked leaves for a
+    128 x 64 tensor-core first step."""
+    net = kblk_three_node(1710)
+    want = kblk_three_node_oracle(1710)
+    got, z, d = run(net, precision=prec, order=order)
+    kst = [st for st in d["steps"] if st["kblk"]]
+    assert len(kst) == 1 and kst[0]["log2_k"] == 16 and kst[0]["class"] == "tcgen05", d["steps"]
+    if prec == "bf16x3":
+        # 4^9 terms per probability with heavy cancellation (probabilities of
+        # either sign): the FP32 gate holds, and the total
+        # variation stays within the split-BF16 bound (operands exact to
+        # about 2^-16, so 2^-15 per step on the absolute terms)
+        assert np.abs(got - want).max() <= FP32_ATOL
+        check_tv(got, want, tv=len(d["steps"]) * 2.0 ** -15 * abs_mass(net))
     else:
         check_tc(prec, got, net, d, want)
 
