@@ -180,7 +180,9 @@ TQC_API tqc_status tqc_plan_step(tqc_plan_t plan, int32_t step, int32_t *log2_m,
  * Plan summary as JSON in buf (NUL-terminated, truncated to size).  Returns
  * the full length needed, excluding the NUL, or -1 on a bad handle.  Each
  * step lists its shape, class, precision, result layout, tile configuration
- * and "ksplit" (K ranges run by separate CTAs, 1 = none).  The first
+ * "ksplit" (K ranges run by separate CTAs, 1 = none) and "kblk" (1 = its
+ * operands are stored K-blocked, [K / 64][rows][64], for rows over 64 KB;
+ * fixed by the plan).  The first
  * contract sets tiles and splits (0 and 1 before it); the autotuner may
  * change them.
  */
