@@ -262,7 +262,9 @@ TQC_API tqc_status tqc_plan_destroy(tqc_plan_t plan);
  * Same result as tqc_contract for the same plan and tensors, but every
  * intermediate lives in one file-scope device array of
  * tqc_noalloc_scratch_bytes() bytes (16 MiB), which every GPU that loads the
- * library holds until the process exits.  The call allocates nothing.
+ * library holds until the process exits.  The call allocates nothing: it
+ * takes the default tile of every step, never autotunes (whatever the plan's
+ * autotune option) and never splits K.
  *   plan      : from tqc_plan; its network may be shape-only (data == NULL)
  *   d_tensors : m device pointers, caller-owned, subcircuit j in the layout of
  *               tqc_subcircuit.data, element type in_dtype (TQC_F64/TQC_F32)

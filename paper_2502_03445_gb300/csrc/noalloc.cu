@@ -119,6 +119,7 @@ extern "C" tqc_status tqc_contract_noalloc(tqc_plan_t plan, const void *const *d
     const uint64_t sv_zver = p.z_version;
     p.z_version = 0;  // the caller's tensors: always compute the total mass
     const int sv_profile = p.profile;
+    const int sv_autotune = p.autotune;  // no tile timing here: it would allocate (events, K-split partials)
     const int sv_device = net.device;
     for (size_t i = 0; i < p.steps.size(); ++i) {
         sv_tiles[i] = p.steps[i].tile;
@@ -129,6 +130,7 @@ extern "C" tqc_status tqc_contract_noalloc(tqc_plan_t plan, const void *const *d
     p.d_ws = (char *)base + ws_off;
     p.ready = true;
     p.profile = 0;
+    p.autotune = 0;
     net.device = dev;
     for (auto &st : p.steps) {  // the tile rule of the allocating path, unsplit (no partials buffer)
         st.tile = default_step_tile(st, step_out_esize(p, st));
@@ -146,6 +148,7 @@ extern "C" tqc_status tqc_contract_noalloc(tqc_plan_t plan, const void *const *d
     p.ready = sv_ready;
     p.z_version = sv_zver;
     p.profile = sv_profile;
+    p.autotune = sv_autotune;
     net.device = sv_device;
     for (size_t i = 0; i < p.steps.size(); ++i) {
         p.steps[i].tile = sv_tiles[i];
