@@ -71,3 +71,36 @@ def test_matches_allocating_entry_point_twice(precision, sliced):
     hs.close()
     ref_plan.close()
     h.close()
+
+
+@pytest.mark.gpu
+def test_ignores_autotune_and_k_split():
+    """A plan that asks for the autotuner, on a network whose deep-K final
+    step the allocating entry point splits along K: the allocation-free call
+    does neither (both would allocate) and still gives the same result."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.set_device(0)
+    net = tensors.pseudo_physical_network(16, [(0, 1)] * 6, [list(range(8)), list(range(8, 16))], 4300)
+    h = tqc.Network(net)
+    ref_plan = tqc.Plan(h, precision="bf16x3")
+    ref = torch.empty(ref_plan.out_elems, dtype=torch.float32, device="cuda")
+    ref_plan.contract(ref)
+    torch.cuda.synchronize()
+    assert ref_plan.describe()["steps"][-1]["ksplit"] > 1
+    ref_np = ref.cpu().numpy().astype(np.float64)
+    hs = tqc.Network(net, shape_only=True)
+    plan = tqc.Plan(hs, precision="bf16x3", autotune=1)
+    d_tensors = [torch.from_numpy(np.ascontiguousarray(nd.data)).cuda() for nd in net.nodes]
+    out = torch.full((plan.out_elems,), float("nan"), dtype=torch.float32, device="cuda")
+    plan.contract_noalloc(d_tensors, out)
+    torch.cuda.synchronize()
+    d = plan.describe()
+    assert d["tuned"] == 0 and all(st["ksplit"] == 1 for st in d["steps"]), d["steps"]
+    err = np.abs(out.cpu().numpy().astype(np.float64) - ref_np).max()
+    assert err <= FP32_ATOL and err <= 1e-4 * np.abs(ref_np).max(), err
+    plan.close()
+    hs.close()
+    ref_plan.close()
+    h.close()
