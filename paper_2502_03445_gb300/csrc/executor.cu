@@ -358,37 +358,38 @@ tqc_status exec_autotune(Plan *p, void *d_out, int out_dtype, cudaStream_t s) {
     return result;
 }
 
+// Allocates the plan's device state on its first contract.  A failure frees
+// whatever this call allocated, so a later call starts again from nothing.
 tqc_status exec_prepare(Plan *p) {
     if (p->ready) return TQC_OK;
     int dev = -1;
     TQC_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
     if (dev != p->net->device) return fail(TQC_ERR_INVALID, "current device differs from the network's device");
+    auto oom = [&](const std::string &what) {
+        cudaGetLastError();
+        exec_release(p);
+        return fail(TQC_ERR_OOM, what);
+    };
     int64_t zslots = p->n_slices();
-    if (p->ws_bytes > 0) {
-        cudaError_t e = cudaMalloc(&p->d_ws, (size_t)p->ws_bytes);
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            return fail(TQC_ERR_OOM, "workspace of " + std::to_string(p->ws_bytes) + " bytes");
-        }
-    }
+    if (p->ws_bytes > 0 && cudaMalloc(&p->d_ws, (size_t)p->ws_bytes) != cudaSuccess)
+        return oom("workspace of " + std::to_string(p->ws_bytes) + " bytes");
     size_t zb = (size_t)p->zws_bytes + 8 * (size_t)zslots + 256;
-    cudaError_t e = cudaMalloc(&p->d_zws, zb);
+    if (cudaMalloc(&p->d_zws, zb) != cudaSuccess) return oom("total-mass workspace");
+    if (cudaMalloc((void **)&p->d_zinfo, 4 * sizeof(double) + 64) != cudaSuccess) return oom("zinfo");
+    cudaError_t e = cudaMemset(p->d_zinfo, 0, 4 * sizeof(double) + 64);
     if (e != cudaSuccess) {
-        cudaGetLastError();
-        return fail(TQC_ERR_OOM, "total-mass workspace");
+        exec_release(p);
+        return cuda_fail(e, "memset");
     }
-    e = cudaMalloc((void **)&p->d_zinfo, 4 * sizeof(double) + 64);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        return fail(TQC_ERR_OOM, "zinfo");
-    }
-    TQC_CUDA(cudaMemset(p->d_zinfo, 0, 4 * sizeof(double) + 64), "memset");
     // tile choice without autotuning: big tiles for big steps
     for (auto &st : p->steps) {
         st.tile = default_step_tile(st, step_out_esize(*p, st));
     }
     tqc_status kst = update_ksplit(p);
-    if (kst != TQC_OK) return kst;
+    if (kst != TQC_OK) {
+        exec_release(p);
+        return kst;
+    }
     p->ready = true;
     return TQC_OK;
 }
