@@ -335,7 +335,11 @@ TQC_API tqc_status tqc_plan_candidates(tqc_net_t net, const tqc_plan_opts *opts,
  */
 /* The L2 norm over all cut assignments of every output state of subcircuit
  * `sub`: d_norms[i] = sqrt(sum_e T_sub[e][i]^2), i in [0, 2^{n_out}).
- * d_norms: device, FP64, 2^{n_out} entries, caller-owned; stream-ordered. */
+ * d_norms: device, FP64, 2^{n_out} entries, caller-owned; stream-ordered.
+ * Deterministic: the partial sums are added in a fixed order.  When the
+ * output states alone cannot fill the GPU the sum is split over the cut
+ * assignments, with a stream-ordered scratch allocation (cudaMallocAsync) of
+ * a few MB for the partials. */
 TQC_API tqc_status tqc_hss_norms(tqc_net_t net, int32_t sub, double *d_norms, void *cuda_stream);
 /* Select heavy states: norms on the device, then every subcircuit is seeded
  * with its heaviest state and states are added in descending norm (ties:

@@ -4,7 +4,9 @@
 // L2 norm of its entries over all cut assignments e,
 //     ||p_{j,i}|| = sqrt(sum_e T_j[e][i]^2),
 // a column reduction of the [4^c][2^o] node tensor (FP64 partial sums, split
-// over e when 2^o alone cannot fill the GPU).  Step 2 (seed each subcircuit
+// over e when 2^o alone cannot fill the GPU, and then added in a fixed order,
+// so equal tensors give bit-identical norms and ties resolve the same way on
+// every call).  Step 2 (seed each subcircuit
 // with its heaviest state, then add states in descending norm until the
 // product of the per-subcircuit counts reaches s_max) orders a few thousand
 // numbers and runs on the host.  The selected states become a new network
@@ -30,8 +32,8 @@ struct tqc_net {
 namespace tqc {
 namespace {
 
-// sum2[x] += sum_{e in [e0, e1)} T[e][x]^2
-__global__ void hss_sum2_kernel(const void *T, int dtype, int64_t n_x, int64_t e_per, int64_t n_e, double *sum2) {
+// part[y][x] = sum_{e in [e0, e1)} T[e][x]^2 for split y = blockIdx.y
+__global__ void hss_sum2_kernel(const void *T, int dtype, int64_t n_x, int64_t e_per, int64_t n_e, double *part) {
     const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= n_x) return;
     const int64_t e0 = (int64_t)blockIdx.y * e_per;
@@ -50,13 +52,16 @@ __global__ void hss_sum2_kernel(const void *T, int dtype, int64_t n_x, int64_t e
             acc += v * v;
         }
     }
-    if (gridDim.y == 1) sum2[x] = acc;
-    else atomicAdd(&sum2[x], acc);
+    part[(int64_t)blockIdx.y * n_x + x] = acc;
 }
 
-__global__ void hss_sqrt_kernel(double *v, int64_t n) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        v[i] = sqrt(v[i]);
+// norm[x] = sqrt(sum over the splits, in ascending order, of part[y][x])
+__global__ void hss_sqrt_kernel(const double *part, int64_t splits, double *norm, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double v = 0.0;
+        for (int64_t y = 0; y < splits; ++y) v += part[y * n + i];
+        norm[i] = sqrt(v);
+    }
 }
 
 // out[e][r] = r < count ? T[e][states[r]] : 0   (r < 2^k)
@@ -81,13 +86,20 @@ tqc_status node_norms(const Node &nd, double *d_norms, cudaStream_t s) {
     ys = std::min<int64_t>(ys, 65535);
     const int64_t e_per = (n_e + ys - 1) / ys;
     ys = (n_e + e_per - 1) / e_per;
-    if (ys > 1 && cudaMemsetAsync(d_norms, 0, sizeof(double) * n_x, s) != cudaSuccess)
-        return fail(TQC_ERR_CUDA, "hss: clear");
     if (xb > 2147483647ll) return fail(TQC_ERR_UNSUPPORTED, "hss: too many output states");
-    hss_sum2_kernel<<<dim3((unsigned)xb, (unsigned)ys), threads, 0, s>>>(nd.d_data, nd.dtype, n_x, e_per, n_e, d_norms);
+    // one split: the partial sums are the norms' squares, in place; several:
+    // stream-ordered scratch of splits x 2^o partial sums (at most a few MB)
+    double *part = d_norms;
+    if (ys > 1 && cudaMallocAsync((void **)&part, sizeof(double) * (size_t)(ys * n_x), s) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(TQC_ERR_OOM, "hss: partial sums");
+    }
+    hss_sum2_kernel<<<dim3((unsigned)xb, (unsigned)ys), threads, 0, s>>>(nd.d_data, nd.dtype, n_x, e_per, n_e, part);
     const int64_t sb = std::min<int64_t>((n_x + threads - 1) / threads, 16ll * sm_count());
-    hss_sqrt_kernel<<<(unsigned)sb, threads, 0, s>>>(d_norms, n_x);
-    if (cudaGetLastError() != cudaSuccess) return fail(TQC_ERR_CUDA, "hss: norm kernels");
+    hss_sqrt_kernel<<<(unsigned)sb, threads, 0, s>>>(part, ys, d_norms, n_x);
+    cudaError_t e = cudaGetLastError();
+    if (ys > 1) cudaFreeAsync(part, s);
+    if (e != cudaSuccess) return fail(TQC_ERR_CUDA, "hss: norm kernels");
     return TQC_OK;
 }
 
