@@ -153,3 +153,31 @@ def test_contract_on_shape_only_network_fails_cleanly():
     p = tqc.Plan(h)
     st = tqc.lib().tqc_contract(p.handle, None, 16, tqc.F32, None, None)
     assert st == tqc.ERR_INVALID
+
+
+@pytest.mark.parametrize("prec,cuts,expect", [("bf16x3", 8, 1), ("bf16", 8, 1), ("tf32", 8, 1),
+                                              ("bf16x3", 7, 0), ("tf32", 7, 0), ("fp32", 8, 0)])
+def test_k_blocked_layout_rule(prec, cuts, expect):
+    """Tensor-core operands with rows over 64 KB are K-blocked: the three
+    lowest shared cuts (64 elements), then the row bits, then the other
+    shared cuts.  Rows of up to 64 KB, and CUDA-core operands, stay K-major
+    (every shared cut below the row bits).  Both operands list the shared
+    cuts in the same order."""
+    net = Network(16, cuts, [Node(list(range(8)), list(range(cuts)), [0] * cuts, None),
+                             Node(list(range(8, 16)), list(range(cuts)), [1] * cuts, None)])
+    h = tqc.Network(net, shape_only=True)
+    p = tqc.Plan(h, precision=prec)
+    d = p.describe()
+    st = d["steps"][-1]
+    assert st["log2_k"] == 2 * cuts and st["kblk"] == expect, st
+    for t in (st["a"], st["b"]):
+        kinds = [m[0] for m in d["layouts"][t]]
+        if expect:
+            assert kinds == ["c"] * 3 + ["q"] * 8 + ["c"] * (cuts - 3), d["layouts"][t]
+        else:
+            assert kinds == ["c"] * cuts + ["q"] * 8, d["layouts"][t]
+    cuts_a = [m for m in d["layouts"][st["a"]] if m[0] == "c"]
+    cuts_b = [m for m in d["layouts"][st["b"]] if m[0] == "c"]
+    assert cuts_a == cuts_b
+    p.close()
+    h.close()
