@@ -32,6 +32,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "reconstructed probs/s & % of roofline, chosen vs plain FP32 form at <=1e-5 err"
+PLAN_FIELDS = ["log2_m", "log2_n", "log2_k", "class", "tile", "ksplit", "kblk"]
 UNIT = "probs/s"
 WORKLOAD = "grid30: 30 qubits, 4 subcircuits of width 10, 10 cuts, full 2^30 output"
 
@@ -357,8 +358,9 @@ def run_workload(args):
             "config": {"workload": f"{args.workload}: bin of 2^24 states, {net.n_cuts} cuts, "
                                    f"{len(net.nodes)} subcircuits, node tensors drawn bin-restricted",
                        "slices": info["n_slices"], "sliced": desc["sliced"],
-                       "plan": [[s_["log2_m"], s_["log2_n"], s_["log2_k"], s_["class"], s_["tile"]]
-                                for s_ in desc["steps"]],
+                       "plan": [[s_["log2_m"], s_["log2_n"], s_["log2_k"], s_["class"], s_["tile"],
+                                 s_["ksplit"], s_["kblk"]] for s_ in desc["steps"]],
+                       "plan_fields": PLAN_FIELDS,
                        "flops_per_step": info["flops"], "mem_budget_gb": args.mem_budget_gb},
             "tflops_per_step": info["flops"] / (ms / 1e3) / 1e12,
             "roofline": roof, "gpu_launches": desc["launches_per_contract"] * args.steps,
@@ -549,6 +551,7 @@ def main():
     for _ in range(max(args.warmup, 3)):
         plan.contract(out)
     torch.cuda.synchronize()
+    desc = plan.describe()                # tiles and K splits as the first contract set them
     sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 and not args.no_clocks else None
     t_end = time.time() + (0.0 if args.no_clocks else 0.6)   # load the GPU so the sampler sees it
     while time.time() < t_end:
@@ -608,8 +611,9 @@ def main():
             "vs_baseline": None, "dtype": desc["precision"], "data": "synthetic",
             "config": {"workload": WORKLOAD if free is None else
                        WORKLOAD.replace("full 2^30 output", f"bin of the lowest {args.free_qubits} qubits"),
-                       "plan": [[s_["log2_m"], s_["log2_n"], s_["log2_k"], s_["class"]]
-                                                      for s_ in desc["steps"]],
+                       "plan": [[s_["log2_m"], s_["log2_n"], s_["log2_k"], s_["class"], s_["tile"],
+                                 s_["ksplit"], s_["kblk"]] for s_ in desc["steps"]],
+                       "plan_fields": PLAN_FIELDS,
                        "order": desc["order"], "instance_seed": "2000 + rank",
                        "l2": "working set 4.6 GB > 129 MB L2, no flush needed",
                        "parallelism": f"weak x{ws}, one network per GPU"},
