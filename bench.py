@@ -540,9 +540,17 @@ def main():
     from paper_2502_03445_gb300 import shard, tqc
 
     net = workloads.grid30(rank)          # weak scaling: one independent network per rank
+    # upload (tensors to HBM) and planning (host only) are timed apart from the steps
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
     h = tqc.Network(net)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
     free = None if args.free_qubits >= net.n_qubits else list(range(args.free_qubits))
     plan = tqc.Plan(h, precision=args.precision, free_qubits=free)
+    t2 = time.perf_counter()
+    setup = {"upload_ms": 1e3 * (t1 - t0), "upload_bytes": int(sum(nd.data.nbytes for nd in net.nodes)),
+             "planning_ms": 1e3 * (t2 - t1)}
     desc = plan.describe()
     out = torch.empty(plan.out_elems, dtype=torch.float32, device="cuda")
     probs_per_step = plan.out_elems
@@ -618,7 +626,7 @@ def main():
                        "l2": "working set 4.6 GB > 129 MB L2, no flush needed",
                        "parallelism": f"weak x{ws}, one network per GPU"},
             "roofline": roof, "gpu_launches": desc["launches_per_contract"] * args.steps,
-            "clocks": clocks}
+            "clocks": clocks, "setup": setup}
 
     # plain FP32 CUDA-core form on the same network
     if not args.no_plain:
