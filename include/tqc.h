@@ -26,6 +26,10 @@
  *     tqc_contract on a plan (which allocates the plan's workspace), further
  *     calls with z_out == NULL neither allocate nor synchronise.
  *   - Handles are not thread-safe: one thread uses a plan at a time.
+ *   - A plan's workspace (and its K-split partials) serve every call on it:
+ *     calls on the same plan must not overlap on the GPU (issue them on one
+ *     stream, or order the streams with events).  Different plans may run
+ *     concurrently.
  */
 #ifndef TQC_H_
 #define TQC_H_
