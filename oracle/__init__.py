@@ -183,3 +183,6 @@ def timed_sample(net, states, n_threads: int = 0):
     t0 = time.perf_counter()
     p = recon_states(net, states, n_threads)
     return p, time.perf_counter() - t0
+
+
+from .bin_pairwise import recon_bin_pairwise  # noqa: E402,F401  (oracle C)

@@ -164,3 +164,59 @@ def test_planted_mistakes_are_caught(mutation):
         if np.abs(Pg - want).max() > 1e-9:
             caught = True
     assert caught
+
+
+# ---------------------------------------------------------------- oracle C (whole bin, pairwise FP64)
+@pytest.mark.parametrize("name", ["bell_one_cut.json", "x_identity_wire.json"])
+def test_oracle_c_golden_fixtures(name):
+    net, want = load_golden(name)
+    np.testing.assert_allclose(oracle.recon_bin_pairwise(net), want, atol=1e-15)
+
+
+def test_oracle_c_matches_statevector_on_bins():
+    """Full output and bins with fixed bits, against the uncut circuit's
+    statevector (which shares nothing with either oracle)."""
+    net, (n, gates) = workloads.line10()
+    full = sv.probabilities(n, gates)
+    np.testing.assert_allclose(oracle.recon_bin_pairwise(net), full, atol=1e-12, rtol=0)
+    for free, ones in (([1, 4, 6, 9], [0, 7]), ([0, 2, 3, 5, 8], [9]), ([7], [1, 2, 3])):
+        fixed = np.zeros(n, np.uint8)
+        fixed[ones] = 1
+        P = oracle.recon_bin_pairwise(net, free, fixed)
+        idx = oracle.bin_states(n, free, fixed, np.arange(1 << len(free)))
+        np.testing.assert_allclose(P, full[idx], atol=1e-12, rtol=0)
+
+
+@pytest.mark.parametrize("n,groups", [(6, [[0, 1], [2, 3], [4, 5]]), (7, [[0, 1, 2], [3], [4, 5, 6]])])
+def test_oracle_c_ghz_closed_form(n, groups):
+    net = _cut(*circuits.ghz(n), groups)
+    want = np.zeros(1 << n)
+    want[0] = want[-1] = 0.5
+    np.testing.assert_allclose(oracle.recon_bin_pairwise(net), want, atol=1e-13)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_oracle_c_matches_oracle_a(seed):
+    """Random-data networks (no physics), random bins: oracle C equals the
+    brute-force formula entry by entry."""
+    rng = np.random.Generator(np.random.PCG64(700 + seed))
+    n = 11 + seed % 3
+    net = tensors.random_data_network(
+        tensors.shape_matched_network(n, 2 + seed % 4, 3 + seed % 4, 9, seed=700 + seed), seed)
+    for F in (n, n - 3, 1, 0):
+        free = sorted(rng.choice(n, size=F, replace=False).tolist())
+        fixed = rng.integers(0, 2, size=n).astype(np.uint8)
+        c = oracle.recon_bin_pairwise(net, free, fixed)
+        a = oracle.recon_bin(net, free, fixed)
+        assert c.shape == a.shape == (1 << F,)
+        np.testing.assert_allclose(c, a, rtol=1e-11, atol=1e-13 * np.abs(a).max())
+
+
+def test_oracle_c_zero_cuts_and_single_node():
+    rng = np.random.Generator(np.random.PCG64(3))
+    a, b = rng.random(4), rng.random(8)
+    net = Network(5, 0, [Node([3, 1], [], [], a), Node([2, 0, 4], [], [], b)])
+    net.check()
+    np.testing.assert_allclose(oracle.recon_bin_pairwise(net), oracle.recon_bin(net), rtol=1e-15)
+    one = Network(4, 0, [Node([2, 0, 3, 1], [], [], rng.random(16))])
+    np.testing.assert_allclose(oracle.recon_bin_pairwise(one), oracle.recon_bin(one), rtol=1e-15)
