@@ -4,13 +4,23 @@
 Workload: the 30-qubit grid shape -- 4 subcircuits of width 10, 10 cuts,
 pseudo-physical FP64 tensors, every qubit free (the full 2^30 FP32
 probability vector).  One step = one tqc_contract of the whole path (ingest,
-the pairwise steps, total mass Z, renormalisation) with the inputs resident
-in HBM.  Metric: reconstructed probabilities per second, for the chosen form
-(tensor-core split BF16, FP32 accumulate) and, beside it, the plain FP32
-CUDA-core form.
+the pairwise steps, renormalisation by the total mass Z) with the inputs
+resident in HBM.  Z depends on the tensors only: the first contract after
+they change computes it (an FP64 scalar network, under 0.2 ms) and later
+ones reuse it, so the timed steps do not recompute it; the e2e leg uploads
+the tensors every step and so recomputes Z every step.  Metric:
+reconstructed probabilities per second, for the chosen form (tensor-core
+steps, FP32 accumulate) and, beside it, the plain FP32 CUDA-core form.
+
+At one GPU the same JSON line also carries two sub-records, each with its
+own CUDA-event timing, roofline, clock samples and sampled oracle error:
+``tensor_bound`` (one 2^24-state bin of the 48-qubit QAOA network per step,
+tensor-core bound) and ``batched`` (256 independent networks in one
+persistent launch replayed from a CUDA graph, against sequential calls).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
   python bench.py --workload qaoa48|grid64   (tensor-bound bins, one JSON line)
+  python bench.py --batch 256                 (the batched launch, one JSON line)
   python bench.py --hss | --planner-eval      (heavy state selection; learned planner)
 
 Under torchrun each rank reconstructs its own network instance (weak
@@ -67,6 +77,9 @@ def parse():
     ap.add_argument("--pe-train", type=int, default=40)
     ap.add_argument("--pe-test", type=int, default=12)
     ap.add_argument("--pe-candidates", type=int, default=6)
+    ap.add_argument("--no-sub", action="store_true",
+                    help="skip the tensor_bound and batched sub-records of the default line")
+    ap.add_argument("--sub-steps", type=int, default=5, help="timed steps of each sub-record")
     return ap.parse_args()
 
 
@@ -217,19 +230,33 @@ def run_reference(args):
     return 0
 
 
-def run_batch(args):
-    """Batched persistent launch: `--batch` independent networks of uneven
-    sizes reconstructed by one tqc_contract_batch launch replayed from a CUDA
-    graph, against contracting them one after the other."""
+def leaf_bytes(desc, m, src_bytes):
+    """Algorithmic bytes of a plan's ingest: every leaf operand element read
+    once from the node tensor and written once as a 4-byte operand."""
+    tot = 0
+    for lay in desc["layouts"][:m]:
+        bits = sum(2 if x.startswith("c") else 1 for x in lay)
+        tot += (src_bytes + 4) * (1 << bits)
+    return tot
+
+
+def measure_batched(args, count=256, steps=None, warmup=None):
+    """Batched persistent launch: ``count`` independent networks of uneven
+    sizes (n 16-28, 2-8 subcircuits, 2-12 cuts, full 2^n outputs each)
+    reconstructed by one tqc_contract_batch launch replayed from a CUDA
+    graph, against contracting them one after the other.  Raw probabilities
+    (the Gaussian FP32 test tensors can have a total mass near zero)."""
     import torch
+    import oracle
+    from gen import Network as GNet, Node as GNode, workloads
     from paper_2502_03445_gb300 import tqc
-    torch.cuda.set_device(0)
-    from gen import workloads
-    nets, redraws = workloads.batch_recipe(args.batch, args.batch_n_lo, args.batch_n_hi)
+    steps = steps or args.steps
+    warmup = max(3, warmup or args.warmup)
+    nets, redraws = workloads.batch_recipe(count, args.batch_n_lo, args.batch_n_hi)
     hs, plans, outs = [], [], []
     for net in nets:
         h = tqc.Network(net, dtype=tqc.F32)
-        p = tqc.Plan(h, precision=args.precision)
+        p = tqc.Plan(h, precision=args.precision, flags=tqc.FLAG_NO_RENORM)
         o = torch.empty(p.out_elems, dtype=torch.float32, device="cuda")
         p.contract(o)
         hs.append(h)
@@ -243,42 +270,101 @@ def run_batch(args):
     g = torch.cuda.CUDAGraph()
     with torch.cuda.graph(g, stream=s):
         tqc.contract_batch(plans, outs, stream=s)
-    for _ in range(args.warmup):
+    for _ in range(warmup):
+        g.replay()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(torch.cuda.current_device()) if not args.no_clocks else None
+    t_end = time.time() + (0.0 if args.no_clocks else 0.6)
+    while time.time() < t_end:
         g.replay()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
-    for _ in range(args.steps):
+    for _ in range(steps):
         g.replay()
     e1.record()
     torch.cuda.synchronize()
+    clocks = sampler.stop() if sampler else None
     tqc.batch_status()
-    ms = e0.elapsed_time(e1) / args.steps
+    ms = e0.elapsed_time(e1) / steps
     # the same work as separate tqc_contract calls
     for _ in range(2):
         for p, o in zip(plans, outs):
             p.contract(o)
     torch.cuda.synchronize()
+    n_seq = max(2, steps // 2)
     e0.record()
-    for _ in range(max(1, args.steps // 2)):
+    for _ in range(n_seq):
         for p, o in zip(plans, outs):
             p.contract(o)
     e1.record()
     torch.cuda.synchronize()
-    ms_seq = e0.elapsed_time(e1) / max(1, args.steps // 2)
-    classes = {}
-    for p in plans:
-        for st in p.describe()["steps"]:
+    ms_seq = e0.elapsed_time(e1) / n_seq
+    g.replay()
+    torch.cuda.synchronize()
+    tqc.batch_status()
+    classes, alg_bytes = {}, 0
+    descs = [p.describe() for p in plans]
+    for net, d in zip(nets, descs):
+        for i, st in enumerate(d["steps"]):
             classes[st["class"]] = classes.get(st["class"], 0) + 1
-    line = {"metric": METRIC, "value": units / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": args.precision, "data": "synthetic (Gaussian tensors, timing only)",
-            "config": {"workload": f"batch: {len(nets)} networks, n ~ U{{{args.batch_n_lo}..{args.batch_n_hi}}}, "
-                                   f"m ~ U{{2..8}}, |E| ~ U{{max(2,m-1)..12}}, full 2^n outputs, one persistent "
-                                   f"launch replayed from a CUDA graph",
-                       "outputs": units, "redraws": redraws, "step_classes": classes},
+            alg_bytes += step_bytes(st, 4)
+        alg_bytes += leaf_bytes(d, len(net.nodes), 4) if d["steps"] else 8 * (1 << net.n_qubits)
+    hbm = peaks()[0]
+    achieved = alg_bytes / (ms / 1e3) / 1e9
+    # sampled check: two states of every fourth network against oracle A,
+    # against the bound of the plan's arithmetic (n_steps 2^-12 of the mean
+    # absolute term mass per state)
+    rng = np.random.Generator(np.random.PCG64(21))
+    worst, max_abs, n_chk = 0.0, 0.0, 0
+    for k in range(0, len(nets), 4):
+        net, p, o = nets[k], plans[k], outs[k]
+        idx = sorted(set(int(i) for i in rng.integers(0, 1 << net.n_qubits, size=2)))
+        want = oracle.recon_states(net, idx)
+        got = o[torch.tensor(idx, device="cuda")].double().cpu().numpy()
+        a = GNet(net.n_qubits, net.n_cuts,
+                 [GNode(nd.out_qubits, nd.cut_ids, nd.cut_role, np.abs(nd.data)) for nd in net.nodes])
+        scale = oracle.total_mass(a) / float(1 << net.n_qubits)
+        n_steps = max(len(descs[k]["steps"]), 1)
+        err = float(np.abs(got - want).max())
+        worst = max(worst, err / (n_steps * 2.0 ** -12 * scale))
+        max_abs = max(max_abs, err)
+        n_chk += len(idx)
+    for p in plans:
+        p.close()
+    for h in hs:
+        h.close()
+    del outs, g
+    torch.cuda.empty_cache()
+    return {"workload": f"batch: {len(nets)} networks, n ~ U{{{args.batch_n_lo}..{args.batch_n_hi}}}, "
+                        f"m ~ U{{2..8}}, |E| ~ U{{max(2,m-1)..12}}, full 2^n outputs (raw, FP32 Gaussian "
+                        f"tensors), one persistent launch replayed from a CUDA graph",
+            "value": units / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "steps": steps, "warmup": warmup,
+            "outputs": units, "redraws": redraws, "step_classes": classes, "gpu_launches": steps,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                         "frac": achieved / hbm, "traffic": None,
+                         "kernel": "batch_kernel (the whole launch)",
+                         "algorithmic_bytes_per_launch": alg_bytes,
+                         "peak_kind": f"{peaks()[3]} copy bandwidth"},
+            "clocks": clocks,
             "sequential_contracts": {"ms_per_step": ms_seq, "value": units / (ms_seq / 1e3),
-                                     "speedup_of_batched": ms_seq / ms}}
+                                     "speedup_of_batched": ms_seq / ms},
+            "error_vs_oracle": {"states": n_chk, "oracle": "A", "max_abs": max_abs,
+                                "max_err_over_bound": worst,
+                                "bound": "n_steps * 2^-12 * mean |term| mass per state"}}
+
+
+def run_batch(args):
+    import torch
+    torch.cuda.set_device(0)
+    r = measure_batched(args, count=args.batch)
+    line = {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": 1, "steps": r["steps"],
+            "warmup": r["warmup"], "ms_per_step": r["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": args.precision, "data": "synthetic (Gaussian tensors)",
+            "config": {"workload": r["workload"], "outputs": r["outputs"], "redraws": r["redraws"],
+                       "step_classes": r["step_classes"]},
+            "roofline": r["roofline"], "clocks": r["clocks"], "gpu_launches": r["gpu_launches"],
+            "sequential_contracts": r["sequential_contracts"], "error_vs_oracle": r["error_vs_oracle"]}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -311,20 +397,33 @@ def path_roofline(steps, n_slices, hbm, bf16):
     return t * n_slices * 1e3
 
 
-def run_workload(args):
-    """One 2^24-state bin of the 48-qubit QAOA network or of the 64-qubit
-    grid shape, sliced to the memory budget: these plans end in tensor-bound
-    steps (K = 4^7..4^9 after slicing), so the roofline is the tensor pipe."""
+def measure_tensor_bound(args, workload="qaoa48", steps=None, warmup=None):
+    """One 2^24-state bin of the 48-qubit QAOA network (or of the 64-qubit
+    grid shape) per step, sliced to the memory budget: these plans end in
+    tensor-bound steps (K = 4^7..4^9 after slicing), so the roofline is the
+    tensor pipe of the dominant step, quoted against the peak of its own
+    precision and against the raw measured BF16 burst."""
     import torch
     from gen import workloads
     from paper_2502_03445_gb300 import tqc
     import oracle
-    torch.cuda.set_device(0)
-    net = workloads.qaoa48(0) if args.workload == "qaoa48" else workloads.grid64_bin(0, 0)
+    steps = steps or args.steps
+    warmup = max(3, warmup or args.warmup)
+    net = workloads.qaoa48(0) if workload == "qaoa48" else workloads.grid64_bin(0, 0)
+    spec = ("gen.workloads", "qaoa48", (0,)) if workload == "qaoa48" else ("gen.workloads", "grid64_bin", (0, 0))
     h = tqc.Network(net)
     plan = tqc.Plan(h, precision=args.precision, mem_budget=int(args.mem_budget_gb * (1 << 30)))
     out = torch.empty(plan.out_elems, dtype=torch.float32, device="cuda")
-    ms = time_plan(torch, plan, out, args.steps, args.warmup, profile=True)
+    for _ in range(warmup):
+        plan.contract(out)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(torch.cuda.current_device()) if not args.no_clocks else None
+    t_end = time.time() + (0.0 if args.no_clocks else 0.6)
+    while time.time() < t_end:
+        plan.contract(out)
+    torch.cuda.synchronize()
+    ms = time_plan(torch, plan, out, steps, 0, profile=True)
+    clocks = sampler.stop() if sampler else None
     desc = plan.describe()
     info = plan.info()
     step_ms = [plan.step_time(i)[0] for i in range(len(desc["steps"]))]
@@ -332,42 +431,75 @@ def run_workload(args):
     top = int(np.argmax(step_ms))
     st = desc["steps"][top]
     alg = 2.0 * 2 ** (st["log2_m"] + st["log2_n"] + st["log2_k"])
-    _, bf16, _, peak_kind = peaks()
+    hbm, bf16, bf16_sus, peak_kind = peaks()
     pk, how = tensor_peak(st["prec"], bf16)
     achieved = alg / (step_ms[top] / 1e3) / 1e12
     roof = {"bound": "tensor", "achieved": achieved, "peak": pk, "unit": "TFLOP/s", "frac": achieved / pk,
             "traffic": None, "peak_kind": f"{peak_kind}: {how}",
             "kernel": f"umma_step (step {top}: log2 M,N,K = {st['log2_m']},{st['log2_n']},{st['log2_k']}, "
-                      f"tile {st['tile']})",
+                      f"{st['prec']}, tile {st['tile']}, ksplit {st['ksplit']})",
             "algorithmic_flops_per_launch": alg, "mean_launch_ms": step_ms[top], "step_ms": step_ms,
+            "frac_of_bf16_burst": achieved / bf16,
             "tensor_pipe_issue_frac_of_bf16": achieved * (3 if st["prec"] == "bf16x3" else 1) / bf16}
-    hbm = peaks()[0]
+    if bf16_sus:
+        roof["frac_of_bf16_sustained"] = achieved / bf16_sus
     roof["path_roofline_ms"] = path_roofline(desc["steps"], info["n_slices"], hbm, bf16)
     roof["path_frac"] = roof["path_roofline_ms"] / ms
-    # sampled check and CPU baseline: oracle B, one state at a time
-    rng = np.random.Generator(np.random.PCG64(5))
-    states = [int(x) for x in rng.integers(0, 1 << net.n_qubits, size=4)]
-    t0 = time.perf_counter()
-    want = oracle.recon_states_elim(net, states)
-    t_cpu = time.perf_counter() - t0
+    got = out.double().cpu().numpy()
+    # sampled check: a sub-bin of 2^8 states by oracle C, and four uniformly
+    # drawn states by oracle B
     z = oracle.total_mass(net)
-    got = out.double().cpu().numpy()[states]
-    line = {"metric": METRIC, "value": plan.out_elems / (ms / 1e3), "unit": UNIT, "n_gpus": 1,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": desc["precision"], "data": "synthetic",
-            "config": {"workload": f"{args.workload}: bin of 2^24 states, {net.n_cuts} cuts, "
-                                   f"{len(net.nodes)} subcircuits, node tensors drawn bin-restricted",
-                       "slices": info["n_slices"], "sliced": desc["sliced"],
-                       "plan": [[s_["log2_m"], s_["log2_n"], s_["log2_k"], s_["class"], s_["tile"],
-                                 s_["ksplit"], s_["kblk"]] for s_ in desc["steps"]],
-                       "plan_fields": PLAN_FIELDS,
-                       "flops_per_step": info["flops"], "mem_budget_gb": args.mem_budget_gb},
-            "tflops_per_step": info["flops"] / (ms / 1e3) / 1e12,
-            "roofline": roof, "gpu_launches": desc["launches_per_contract"] * args.steps,
-            "sampled_max_abs_err": float(np.abs(got - want / z).max()),
-            "cpu_baseline": {"value": len(states) / t_cpu, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-                             "sample": f"{len(states)} states, oracle B (FP64 pairwise elimination per state; "
-                                       f"numpy tensordot, BLAS threads up to the host's cores)"}}
+    rng = np.random.Generator(np.random.PCG64(5))
+    sub_free = sorted(int(q) for q in rng.choice(net.n_qubits, size=8, replace=False))
+    fixed = rng.integers(0, 2, size=net.n_qubits).astype(np.uint8)
+    idx_c = np.array(oracle.bin_states(net.n_qubits, sub_free, fixed, np.arange(256)), dtype=np.int64)
+    t0 = time.perf_counter()
+    want_c = oracle.recon_bin_pairwise(net, sub_free, fixed) / z
+    t_c = time.perf_counter() - t0
+    idx_b = [int(x) for x in rng.integers(0, 1 << net.n_qubits, size=4)]
+    t0 = time.perf_counter()
+    want_b = oracle.recon_states_elim(net, idx_b) / z
+    t_b = time.perf_counter() - t0
+    want = np.concatenate([want_c, want_b])
+    err = np.abs(got[np.concatenate([idx_c, np.array(idx_b, dtype=np.int64)])] - want)
+    plan.close()
+    h.close()
+    del out
+    torch.cuda.empty_cache()
+    return {"workload": f"{workload}: bin of 2^24 states, {net.n_cuts} cuts, {len(net.nodes)} subcircuits, "
+                        f"node tensors drawn bin-restricted",
+            "value": (1 << net.n_qubits) / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "steps": steps,
+            "warmup": warmup, "dtype": desc["precision"],
+            "slices": info["n_slices"], "sliced": desc["sliced"],
+            "plan": [[s_["log2_m"], s_["log2_n"], s_["log2_k"], s_["class"], s_["prec"], s_["tile"],
+                      s_["ksplit"], s_["kblk"]] for s_ in desc["steps"]],
+            "plan_fields": PLAN_FIELDS[:4] + ["prec"] + PLAN_FIELDS[4:],
+            "flops_per_step": info["flops"], "tflops_per_step": info["flops"] / (ms / 1e3) / 1e12,
+            "mem_budget_gb": args.mem_budget_gb,
+            "roofline": roof, "clocks": clocks, "gpu_launches": desc["launches_per_contract"] * steps,
+            "error_vs_oracle": {"states": int(len(want)), "max_abs": float(err.max()),
+                                "tv_over_checked": float(0.5 * err.sum() / np.abs(want).sum()),
+                                "sample": "a 2^8-state sub-bin (oracle C) and 4 uniformly drawn states (oracle B)"},
+            "cpu_baseline": {"value": (256 + len(idx_b)) / (t_c + t_b), "unit": UNIT, "cores": os.cpu_count(),
+                             "kind": "oracle",
+                             "sample": f"256 states of a sub-bin by oracle C ({t_c:.1f} s) and {len(idx_b)} states "
+                                       f"by oracle B ({t_b:.1f} s), numpy FP64, BLAS threads up to the host's cores"},
+            "_spec": spec}
+
+
+def run_workload(args):
+    import torch
+    torch.cuda.set_device(0)
+    r = measure_tensor_bound(args, args.workload)
+    r.pop("_spec")
+    line = {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": 1, "steps": r["steps"],
+            "warmup": r["warmup"], "ms_per_step": r["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": r["dtype"], "data": "synthetic",
+            "config": {k: r[k] for k in ("workload", "slices", "sliced", "plan", "plan_fields", "flops_per_step",
+                                         "mem_budget_gb")},
+            "tflops_per_step": r["tflops_per_step"], "roofline": r["roofline"], "clocks": r["clocks"],
+            "gpu_launches": r["gpu_launches"], "error_vs_oracle": r["error_vs_oracle"],
+            "cpu_baseline": r["cpu_baseline"]}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -668,10 +800,18 @@ def main():
         line["e2e"] = {"value": e2e_probs / t_e2e, "unit": UNIT,
                        "h2d_bytes_per_step": int(sum(x.numel() * 8 for x in hin)),
                        "d2h_bytes_per_step": int(hout.numel() * 4), "ms_per_step": 1e3 * t_e2e}
-    if rank == 0:
-        print(json.dumps(line), flush=True)
     plan.close()
     h.close()
+    del out
+    torch.cuda.empty_cache()
+    # sub-records at one GPU: the tensor-bound bin and the batched launch
+    if ws == 1 and not args.no_sub:
+        tb = measure_tensor_bound(args, "qaoa48", steps=args.sub_steps, warmup=args.warmup)
+        tb.pop("_spec")
+        line["tensor_bound"] = tb
+        line["batched"] = measure_batched(args, 256, steps=args.sub_steps, warmup=args.warmup)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
     if ws > 1:
         dist.destroy_process_group()
     return 0

@@ -65,7 +65,10 @@ enum { TQC_F64 = 0, TQC_F32 = 1 };
 enum {
     TQC_PREC_FP32 = 0,   /* plain form: every step on CUDA cores in FP32 */
     TQC_PREC_TF32 = 1,   /* dense steps on tcgen05 tensor cores, TF32 inputs, FP32 accumulate */
-    TQC_PREC_BF16 = 2,   /* dense steps on tcgen05, BF16 inputs, FP32 accumulate */
+    TQC_PREC_BF16 = 2,   /* dense steps on tcgen05, BF16 inputs, FP32 accumulate.  Does NOT meet the
+                            1e-3 total-variation gate of the tensor-core forms on pseudo-physical
+                            inputs (measured 1.2e-3 to 1.6e-3: operands keep 8 significant bits);
+                            offered for speed comparisons, never chosen by TQC_PREC_AUTO */
     TQC_PREC_BF16X3 = 3, /* dense steps on tcgen05, split BF16 (hi*hi + hi*lo + lo*hi), FP32 accumulate */
     TQC_PREC_AUTO = 4    /* library's choice (currently BF16X3) */
 };
@@ -203,6 +206,11 @@ TQC_API int32_t tqc_plan_describe(tqc_plan_t plan, char *buf, int32_t size);
  * Steps: bin restriction and layout (ingest), the pairwise contractions,
  * FP64 sum over slices, renormalisation by Z.  The first call allocates the
  * plan's workspace.
+ * Device-side failures: every wait of a tensor-core step is bounded; one that
+ * gives up sets the plan's error word and its output is wrong.  The word is
+ * read only by a call with a non-NULL z_out: that call returns
+ * TQC_ERR_TIMEOUT if any call on the plan since the last such report gave up,
+ * and clears the word.  Calls with z_out == NULL never report it.
  */
 TQC_API tqc_status tqc_contract(tqc_plan_t plan, const uint8_t *fixed_bits, void *d_out, int32_t out_dtype,
                                 double *z_out, void *cuda_stream);
@@ -243,6 +251,14 @@ TQC_API tqc_status tqc_batch_status(void *cuda_stream);
  * must give up (about one second) and tqc_batch_status must report it. */
 TQC_API tqc_status tqc_batch_inject_stall(int32_t enable);
 
+/* Fault-injection hook for tests: while enabled, every tensor-core step
+ * launched by tqc_contract or tqc_contract_noalloc has its first CTA skip
+ * its first operand copy, so that CTA's MMA issuer gives up waiting (about
+ * two seconds), drains, frees its tensor memory and sets the error word:
+ * the call then reports TQC_ERR_TIMEOUT as described for each entry point.
+ * Nothing faults; the output of such a call is wrong. */
+TQC_API tqc_status tqc_step_inject_stall(int32_t enable);
+
 /*
  * Per-step device timing (for roofline reporting).  enable = 1 makes every
  * following tqc_contract record a CUDA event pair, on the caller's stream,
@@ -277,8 +293,14 @@ TQC_API tqc_status tqc_plan_destroy(tqc_plan_t plan);
  * Returns TQC_ERR_UNSUPPORTED, before any device work, when the plan needs
  * more scratch than the array holds.  All calls share the array: calls that
  * overlap on the GPU (other streams, other threads) race and corrupt each
- * other.  The first call on a device looks the array's address up with
+ * other.  The call reads and changes none of the plan's or the network's
+ * own device state, so tqc_contract on the same plan is unaffected.  The
+ * first call on a device looks the array's address up with
  * cudaGetSymbolAddress; make that first call before any stream capture.
+ * Each call ends by copying its 4-byte error word into a host stack
+ * variable, so it synchronises cuda_stream; it returns TQC_ERR_TIMEOUT when
+ * a bounded wait of one of its tensor-core steps gave up (the output is then
+ * wrong).
  */
 TQC_API tqc_status tqc_contract_noalloc(tqc_plan_t plan, const void *const *d_tensors, int32_t in_dtype,
                                         const uint8_t *fixed_bits, void *d_out, int32_t out_dtype,

@@ -186,3 +186,4 @@ def timed_sample(net, states, n_threads: int = 0):
 
 
 from .bin_pairwise import recon_bin_pairwise  # noqa: E402,F401  (oracle C)
+from .pool import recon_states_elim_pool  # noqa: E402,F401  (oracle B over spawned processes)

@@ -52,11 +52,13 @@ int src_pos_cut(const Node &nd, int c) {
 
 // Ingest arguments of leaf j for slice `slice` (fixed output bits of the bin
 // plus sliced cut values go to src_base).
-IngestArgs leaf_args(const Plan &p, const TensorPlan &t, int j, const uint8_t *fixed, int64_t slice, bool zplan) {
+IngestArgs leaf_args(const Plan &p, const TensorPlan &t, int j, const uint8_t *fixed, int64_t slice, bool zplan,
+                     const ExecCtx *c = nullptr) {
     const Node &nd = p.net->nodes[j];
     IngestArgs g;
-    g.src = nd.d_data;
-    g.src_dtype = nd.dtype;
+    const bool caller = c && c->node_data;
+    g.src = caller ? c->node_data[j] : nd.d_data;
+    g.src_dtype = caller ? c->node_dtype : nd.dtype;
     int64_t base = 0;
     if (!zplan) {
         std::vector<char> isfree(p.net->n_qubits, 0);
@@ -431,6 +433,132 @@ void exec_release(Plan *p) {
     p->ready = false;
 }
 
+// The launch sequence of one contract.  Everything it reads and writes
+// besides the caller's output comes from `c`.
+tqc_status exec_run(Plan &pl, const ExecCtx &c, const uint8_t *fixed_bits, void *d_out, int out_dtype, void *stream,
+                    bool *z_computed) {
+    Plan *p = &pl;
+    cudaStream_t s = (cudaStream_t)stream;
+    tqc_status st = TQC_OK;
+    if (z_computed) *z_computed = false;
+    const uint8_t *fixed = fixed_bits ? fixed_bits : p->fixed_bits.data();
+    if (fixed_bits)
+        for (int q = 0; q < p->net->n_qubits; ++q)
+            if (fixed_bits[q] > 1) return fail(TQC_ERR_INVALID, "fixed_bits entries must be 0 or 1");
+    const int64_t ns = p->n_slices();
+    const int nE = p->net->n_cuts;
+    double *zslice = (double *)ws_ptr(c.zws, p->zws_bytes);
+    // a step's tile: the plan's (autotuned or default), or the default and unsplit
+    auto step_of = [&](const StepPlan &sp) {
+        StepPlan x = sp;
+        if (c.default_tiles) {
+            x.tile = default_step_tile(sp, step_out_esize(*p, sp));
+            x.ksplit = 1;
+        }
+        return x;
+    };
+
+    // ---- total mass Z (scalar network: every output summed), FP64.  Z depends
+    // on the tensors only, so the allocating path recomputes it only when they
+    // changed since the plan last computed it.
+    if (c.compute_z) {
+        for (int64_t sl = 0; sl < ns; ++sl) {
+            for (int j = 0; j < p->m; ++j) {
+                const TensorPlan &t = p->ztensors[j];
+                IngestArgs g = leaf_args(*p, t, j, fixed, sl, true, &c);
+                g.dst = p->m == 1 ? (void *)(zslice + sl) : (void *)ws_ptr(c.zws, t.offset);
+                TQC_CUDA(launch_ingest(g, (int64_t)1 << t.nbits(), s), "total-mass ingest");
+            }
+            for (size_t i = 0; i < p->zsteps.size(); ++i) {
+                const StepPlan &zs = p->zsteps[i];
+                StepArgs a = step_args(*p, p->ztensors, zs, c.zws, simt_f64_tile());
+                a.epi.mode = EPI_Z;
+                a.epi.out = zs.final ? (void *)(zslice + sl) : (void *)ws_ptr(c.zws, p->ztensors[zs.c].offset);
+                TQC_CUDA(launch_simt_step_f64(a, s), "total-mass step");
+            }
+        }
+        TQC_CUDA(launch_zfinal(zslice, (int)ns, nE, !(p->flags & TQC_FLAG_NO_RENORM), c.zinfo, s), "zfinal");
+        if (z_computed) *z_computed = true;
+    }
+
+    // ---- single subcircuit: the bin is a gather of its tensor
+    if (p->m == 1) {
+        const TensorPlan &t = p->tensors[0];
+        IngestArgs g = leaf_args(*p, t, 0, fixed, 0, false, &c);
+        g.dst = d_out;
+        g.scaled = 1;
+        g.out_f64 = out_dtype == TQC_F64;
+        g.zinfo = c.zinfo;
+        TQC_CUDA(launch_ingest(g, p->out_elems(), s), "ingest");
+        return TQC_OK;
+    }
+    const bool sliced = ns > 1;
+    double *acc = nullptr;
+    if (sliced) acc = out_dtype == TQC_F64 ? (double *)d_out : (double *)ws_ptr(c.ws, p->acc_offset);
+    int *d_err = (int *)(c.zinfo + 2);
+    for (int64_t sl = 0; sl < ns; ++sl) {
+        for (int j = 0; j < p->m; ++j) {
+            const TensorPlan &t = p->tensors[j];
+            if (sl > 0 && !t.slice_dep) continue;
+            IngestArgs g = leaf_args(*p, t, j, fixed, sl, false, &c);
+            g.dst = ws_ptr(c.ws, t.offset);
+            if (t.storage == ST_BF16X2) g.dst_lo = ws_ptr(c.ws, t.offset + t.plane_bytes);
+            g.storage = t.storage;
+            TQC_CUDA(launch_ingest(g, (int64_t)1 << t.nbits(), s), "ingest");
+        }
+        for (size_t si = 0; si < p->steps.size(); ++si) {
+            const StepPlan sp = step_of(p->steps[si]);
+            if (sl > 0 && !p->tensors[sp.c].slice_dep) continue;
+            StepArgs a = step_args(*p, p->tensors, sp, c.ws, tile_of(sp));
+            const TensorPlan &tc = p->tensors[sp.c];
+            a.epi.zinfo = c.zinfo;
+            if (sp.final) {
+                if (sliced) {
+                    a.epi.out = acc;
+                    a.epi.mode = sl == 0 ? EPI_F64_SET : EPI_F64_ADD;
+                } else {
+                    a.epi.out = d_out;
+                    a.epi.mode = out_dtype == TQC_F64 ? EPI_OUT_F64 : EPI_OUT_F32;
+                }
+            } else {
+                a.epi.out = ws_ptr(c.ws, tc.offset);
+                if (tc.storage == ST_BF16X2) a.epi.out_lo = ws_ptr(c.ws, tc.offset + tc.plane_bytes);
+                a.epi.mode = epi_mode_of(tc.storage);
+            }
+            cudaEvent_t ev[2] = {nullptr, nullptr};
+            if (c.profile) {
+                TQC_CUDA(cudaEventCreate(&ev[0]), "event");
+                TQC_CUDA(cudaEventCreate(&ev[1]), "event");
+                TQC_CUDA(cudaEventRecord(ev[0], s), "event record");
+            }
+            if (sp.ksplit > 1) {
+                // split K: FP32 partials, then one pass into the step's own output mode
+                void *out = a.epi.out;
+                const int mode = a.epi.mode;
+                a.ksplit = sp.ksplit;
+                a.split_stride = p->out_elems();
+                a.epi.out = c.kpart;
+                a.epi.mode = EPI_F32;
+                st = launch_step(*p, sp, a, d_err, s);
+                if (st != TQC_OK) return st;
+                TQC_CUDA(launch_ksplit_reduce((const float *)c.kpart, sp.ksplit, p->out_elems(), mode, out, c.zinfo,
+                                              s),
+                         "K-split reduce");
+            } else {
+                st = launch_step(*p, sp, a, d_err, s);
+                if (st != TQC_OK) return st;
+            }
+            if (c.profile) {
+                TQC_CUDA(cudaEventRecord(ev[1], s), "event record");
+                if (p->step_events.size() < p->steps.size()) p->step_events.resize(p->steps.size());
+                p->step_events[si].push_back({(void *)ev[0], (void *)ev[1]});
+            }
+        }
+    }
+    if (sliced) TQC_CUDA(launch_finalize(acc, d_out, out_dtype == TQC_F64, c.zinfo, p->out_elems(), s), "finalize");
+    return TQC_OK;
+}
+
 tqc_status exec_contract(Plan *p, const uint8_t *fixed_bits, void *d_out, int out_dtype, double *z_out,
                          void *stream) {
     tqc_status st = exec_prepare(p);
@@ -440,118 +568,28 @@ tqc_status exec_contract(Plan *p, const uint8_t *fixed_bits, void *d_out, int ou
         st = exec_autotune(p, d_out, out_dtype, s);
         if (st != TQC_OK) return st;
     }
-    const uint8_t *fixed = fixed_bits ? fixed_bits : p->fixed_bits.data();
-    if (fixed_bits)
-        for (int q = 0; q < p->net->n_qubits; ++q)
-            if (fixed_bits[q] > 1) return fail(TQC_ERR_INVALID, "fixed_bits entries must be 0 or 1");
-    const int64_t ns = p->n_slices();
-    const int nE = p->net->n_cuts;
-    double *zslice = (double *)ws_ptr(p->d_zws, p->zws_bytes);
-
-    // ---- total mass Z (scalar network: every output summed), FP64.  Z depends
-    // on the tensors only, so it is recomputed when they changed since the
-    // plan last computed it.
-    if (p->z_version != p->net->version) {
-    for (int64_t sl = 0; sl < ns; ++sl) {
-        for (int j = 0; j < p->m; ++j) {
-            const TensorPlan &t = p->ztensors[j];
-            IngestArgs g = leaf_args(*p, t, j, fixed, sl, true);
-            g.dst = p->m == 1 ? (void *)(zslice + sl) : (void *)ws_ptr(p->d_zws, t.offset);
-            TQC_CUDA(launch_ingest(g, (int64_t)1 << t.nbits(), s), "total-mass ingest");
-        }
-        for (size_t i = 0; i < p->zsteps.size(); ++i) {
-            const StepPlan &zs = p->zsteps[i];
-            StepArgs a = step_args(*p, p->ztensors, zs, p->d_zws, simt_f64_tile());
-            a.epi.mode = EPI_Z;
-            a.epi.out = zs.final ? (void *)(zslice + sl) : (void *)ws_ptr(p->d_zws, p->ztensors[zs.c].offset);
-            TQC_CUDA(launch_simt_step_f64(a, s), "total-mass step");
-        }
-    }
-    TQC_CUDA(launch_zfinal(zslice, (int)ns, nE, !(p->flags & TQC_FLAG_NO_RENORM), p->d_zinfo, s), "zfinal");
-    p->z_version = p->net->version;
-    }
-
-    // ---- single subcircuit: the bin is a gather of its tensor
-    if (p->m == 1) {
-        const TensorPlan &t = p->tensors[0];
-        IngestArgs g = leaf_args(*p, t, 0, fixed, 0, false);
-        g.dst = d_out;
-        g.scaled = 1;
-        g.out_f64 = out_dtype == TQC_F64;
-        g.zinfo = p->d_zinfo;
-        TQC_CUDA(launch_ingest(g, p->out_elems(), s), "ingest");
-    } else {
-        const bool sliced = ns > 1;
-        double *acc = nullptr;
-        if (sliced) acc = out_dtype == TQC_F64 ? (double *)d_out : (double *)ws_ptr(p->d_ws, p->acc_offset);
-        int *d_err = (int *)(p->d_zinfo + 2);
-        for (int64_t sl = 0; sl < ns; ++sl) {
-            for (int j = 0; j < p->m; ++j) {
-                const TensorPlan &t = p->tensors[j];
-                if (sl > 0 && !t.slice_dep) continue;
-                IngestArgs g = leaf_args(*p, t, j, fixed, sl, false);
-                g.dst = ws_ptr(p->d_ws, t.offset);
-                if (t.storage == ST_BF16X2) g.dst_lo = ws_ptr(p->d_ws, t.offset + t.plane_bytes);
-                g.storage = t.storage;
-                TQC_CUDA(launch_ingest(g, (int64_t)1 << t.nbits(), s), "ingest");
-            }
-            for (const StepPlan &sp : p->steps) {
-                if (sl > 0 && !p->tensors[sp.c].slice_dep) continue;
-                StepArgs a = step_args(*p, p->tensors, sp, p->d_ws, tile_of(sp));
-                const TensorPlan &tc = p->tensors[sp.c];
-                a.epi.zinfo = p->d_zinfo;
-                if (sp.final) {
-                    if (sliced) {
-                        a.epi.out = acc;
-                        a.epi.mode = sl == 0 ? EPI_F64_SET : EPI_F64_ADD;
-                    } else {
-                        a.epi.out = d_out;
-                        a.epi.mode = out_dtype == TQC_F64 ? EPI_OUT_F64 : EPI_OUT_F32;
-                    }
-                } else {
-                    a.epi.out = ws_ptr(p->d_ws, tc.offset);
-                    if (tc.storage == ST_BF16X2) a.epi.out_lo = ws_ptr(p->d_ws, tc.offset + tc.plane_bytes);
-                    a.epi.mode = epi_mode_of(tc.storage);
-                }
-                size_t si = &sp - p->steps.data();
-                cudaEvent_t ev[2] = {nullptr, nullptr};
-                if (p->profile) {
-                    TQC_CUDA(cudaEventCreate(&ev[0]), "event");
-                    TQC_CUDA(cudaEventCreate(&ev[1]), "event");
-                    TQC_CUDA(cudaEventRecord(ev[0], s), "event record");
-                }
-                if (sp.ksplit > 1) {
-                    // split K: FP32 partials, then one pass into the step's own output mode
-                    void *out = a.epi.out;
-                    const int mode = a.epi.mode;
-                    a.ksplit = sp.ksplit;
-                    a.split_stride = p->out_elems();
-                    a.epi.out = p->d_kpart;
-                    a.epi.mode = EPI_F32;
-                    st = launch_step(*p, sp, a, d_err, s);
-                    if (st != TQC_OK) return st;
-                    TQC_CUDA(launch_ksplit_reduce((const float *)p->d_kpart, sp.ksplit, p->out_elems(), mode, out,
-                                                  p->d_zinfo, s),
-                             "K-split reduce");
-                } else {
-                    st = launch_step(*p, sp, a, d_err, s);
-                    if (st != TQC_OK) return st;
-                }
-                if (p->profile) {
-                    TQC_CUDA(cudaEventRecord(ev[1], s), "event record");
-                    if (p->step_events.size() < p->steps.size()) p->step_events.resize(p->steps.size());
-                    p->step_events[si].push_back({(void *)ev[0], (void *)ev[1]});
-                }
-            }
-        }
-        if (sliced) TQC_CUDA(launch_finalize(acc, d_out, out_dtype == TQC_F64, p->d_zinfo, p->out_elems(), s), "finalize");
-    }
+    ExecCtx c;
+    c.ws = p->d_ws;
+    c.zws = p->d_zws;
+    c.zinfo = p->d_zinfo;
+    c.kpart = p->d_kpart;
+    c.compute_z = p->z_version != p->net->version;
+    c.profile = p->profile != 0;
+    bool zc = false;
+    st = exec_run(*p, c, fixed_bits, d_out, out_dtype, stream, &zc);
+    if (st != TQC_OK) return st;
+    if (zc) p->z_version = p->net->version;
     if (z_out) {
+        // Z, the scale and the error word, which stays set from the call whose
+        // bounded wait gave up until a call with z_out reports (and clears) it
         double zi[4];
         TQC_CUDA(cudaMemcpyAsync(zi, p->d_zinfo, sizeof zi, cudaMemcpyDeviceToHost, s), "z copy");
         TQC_CUDA(cudaStreamSynchronize(s), "sync");
         *z_out = zi[0];
-        if (((int *)(zi + 2))[0] != 0) return fail(TQC_ERR_TIMEOUT, "a tensor-core step gave up waiting on its pipeline");
+        if (((int *)(zi + 2))[0] != 0) {
+            TQC_CUDA(cudaMemsetAsync(p->d_zinfo + 2, 0, sizeof(int), s), "error word clear");
+            return fail(TQC_ERR_TIMEOUT, "a tensor-core step gave up waiting on its pipeline");
+        }
     }
     return TQC_OK;
 }

@@ -22,7 +22,10 @@
 //     threads) race on it and give wrong results;
 //   * the first call on a device looks up the array's device address with
 //     cudaGetSymbolAddress (which may load the module); make that first call
-//     before any stream capture.
+//     before any stream capture;
+//   * each call ends by reading its error word back to the host (a 4-byte
+//     copy into a stack variable), so it synchronises the caller's stream and
+//     reports a bounded device wait that gave up as TQC_ERR_TIMEOUT.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -93,66 +96,34 @@ extern "C" tqc_status tqc_contract_noalloc(tqc_plan_t plan, const void *const *d
         base = g_scratch_addr[dev];
     }
     cudaStream_t s = (cudaStream_t)cuda_stream;
-    // The error word in the zinfo block must start at zero on every call;
-    // everything else is written before it is read (operands by ingest,
-    // intermediates by their step, the FP64 slice sum by the first slice, the
-    // per-slice masses by the total-mass network).
+    // The zinfo block (Z, scale, error word) must start at zero on every
+    // call; everything else is written before it is read (operands by
+    // ingest, intermediates by their step, the FP64 slice sum by the first
+    // slice, the per-slice masses by the total-mass network).
     e = cudaMemsetAsync(base, 0, (size_t)zinfo_bytes, s);
     if (e != cudaSuccess) return fail(TQC_ERR_CUDA, std::string("scratch clear: ") + cudaGetErrorString(e));
 
-    // Point the plan's device state and the network's tensors at the scratch
-    // and the caller's tensors for the duration of this call (no heap use:
-    // at most 63 subcircuits and 62 steps).
-    Net &net = *p.net;
-    void *saved_data[64];
-    int saved_dtype[64];
-    int sv_tiles[64], sv_ksplit[64];
-    for (int j = 0; j < p.m; ++j) {
-        saved_data[j] = net.nodes[j].d_data;
-        saved_dtype[j] = net.nodes[j].dtype;
-        net.nodes[j].d_data = const_cast<void *>(d_tensors[j]);
-        net.nodes[j].dtype = in_dtype;
-    }
-    void *sv_ws = p.d_ws, *sv_zws = p.d_zws;
-    double *sv_zinfo = p.d_zinfo;
-    const bool sv_ready = p.ready;
-    const uint64_t sv_zver = p.z_version;
-    p.z_version = 0;  // the caller's tensors: always compute the total mass
-    const int sv_profile = p.profile;
-    const int sv_autotune = p.autotune;  // no tile timing here: it would allocate (events, K-split partials)
-    const int sv_device = net.device;
-    for (size_t i = 0; i < p.steps.size(); ++i) {
-        sv_tiles[i] = p.steps[i].tile;
-        sv_ksplit[i] = p.steps[i].ksplit;
-    }
-    p.d_zinfo = (double *)base;
-    p.d_zws = (char *)base + zws_off;  // the per-slice masses follow the Z network buffers
-    p.d_ws = (char *)base + ws_off;
-    p.ready = true;
-    p.profile = 0;
-    p.autotune = 0;
-    net.device = dev;
-    for (auto &st : p.steps) {  // the tile rule of the allocating path, unsplit (no partials buffer)
-        st.tile = default_step_tile(st, step_out_esize(p, st));
-        st.ksplit = 1;
-    }
-    tqc_status st = exec_contract(&p, fixed_bits, d_out, out_dtype, nullptr, cuda_stream);
-    // restore
-    for (int j = 0; j < p.m; ++j) {
-        net.nodes[j].d_data = saved_data[j];
-        net.nodes[j].dtype = saved_dtype[j];
-    }
-    p.d_ws = sv_ws;
-    p.d_zws = sv_zws;
-    p.d_zinfo = sv_zinfo;
-    p.ready = sv_ready;
-    p.z_version = sv_zver;
-    p.profile = sv_profile;
-    p.autotune = sv_autotune;
-    net.device = sv_device;
-    for (size_t i = 0; i < p.steps.size(); ++i) {
-        p.steps[i].tile = sv_tiles[i];
-        p.steps[i].ksplit = sv_ksplit[i];
-    }
-    return st;
+    // Every buffer of this call is in the scratch array or the caller's: the
+    // plan's and the network's own device state is neither read nor changed,
+    // so other calls on the same plan or network are unaffected.  Tiles are
+    // the default ones, unsplit (the autotuner and the K-split partials would
+    // allocate).
+    ExecCtx c;
+    c.zinfo = (double *)base;
+    c.zws = (char *)base + zws_off;  // the per-slice masses follow the Z network buffers
+    c.ws = (char *)base + ws_off;
+    c.node_data = d_tensors;
+    c.node_dtype = in_dtype;
+    c.default_tiles = true;
+    c.compute_z = true;              // the caller's tensors: always compute the total mass
+    tqc_status st = exec_run(p, c, fixed_bits, d_out, out_dtype, cuda_stream, nullptr);
+    if (st != TQC_OK) return st;
+    // The error word of this call's tensor-core steps: read back into a host
+    // stack variable (no allocation) after the stream has drained.
+    int werr = 0;
+    e = cudaMemcpyAsync(&werr, c.zinfo + 2, sizeof werr, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail(TQC_ERR_CUDA, std::string("noalloc status: ") + cudaGetErrorString(e));
+    if (werr != 0) return fail(TQC_ERR_TIMEOUT, "a tensor-core step gave up waiting on its pipeline");
+    return TQC_OK;
 }

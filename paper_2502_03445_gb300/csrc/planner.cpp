@@ -819,7 +819,8 @@ std::string plan_describe(const Plan &pl) {
     std::ostringstream os;
     os << "{\"m\":" << p->m << ",\"n_qubits\":" << net->n_qubits << ",\"n_cuts\":" << net->n_cuts
        << ",\"free\":" << p->free_qubits.size() << ",\"precision\":\"" << prec_name(p->precision)
-       << "\",\"planner\":\"" << p->planner_used << "\",\"tuned\":" << p->tuned << ",\"sliced\":[";
+       << "\",\"planner\":\"" << p->planner_used << "\",\"tuned\":" << p->tuned
+       << ",\"ready\":" << (p->ready ? 1 : 0) << ",\"sliced\":[";
     for (size_t i = 0; i < p->sliced.size(); ++i) os << (i ? "," : "") << p->sliced[i];
     os << "],\"order\":[";
     for (size_t i = 0; i < p->order.size(); ++i)

@@ -170,8 +170,28 @@ StepCost step_cost(int mb, int nb, int kb, int klass, int prec, const CostConsts
 std::vector<double> plan_features(const Plan &p);   // learned cost-model features
 int choose_class(int mb, int nb, int kb, int prec);
 
+// Where one contract reads and writes.  The allocating path uses the
+// plan's own device state; the allocation-free entry point points every
+// buffer at its fixed scratch array and reads the caller's tensors, so it
+// never touches the plan's or the network's device state.
+struct ExecCtx {
+    void *ws = nullptr;                      // main workspace
+    void *zws = nullptr;                     // total-mass network (per-slice masses follow it)
+    double *zinfo = nullptr;                 // [Z, scale, error word]
+    void *kpart = nullptr;                   // FP32 partials of K-split steps
+    const void *const *node_data = nullptr;  // per subcircuit; NULL = the network's device copies
+    int node_dtype = TQC_F64;                // element type of node_data
+    bool default_tiles = false;              // default tile of every step and no K split
+    bool compute_z = false;                  // compute the total mass (else only when stale)
+    bool profile = false;                    // record per-step events in the plan
+};
+
 // executor entry points (executor.cu)
 tqc_status exec_prepare(Plan *p);
+// The launch sequence of one contract on `stream` (no allocation, no
+// synchronisation).  *z_computed tells whether the total mass was computed.
+tqc_status exec_run(Plan &p, const ExecCtx &c, const uint8_t *fixed_bits, void *d_out, int out_dtype,
+                    void *stream, bool *z_computed);
 tqc_status exec_contract(Plan *p, const uint8_t *fixed_bits, void *d_out, int out_dtype, double *z_out,
                          void *stream);
 void exec_release(Plan *p);

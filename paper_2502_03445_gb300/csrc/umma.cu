@@ -34,6 +34,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <atomic>
 #include <mutex>
 
 #include "device_common.cuh"
@@ -49,6 +50,7 @@ constexpr int EPI_THREADS = 32 * EPI_WARPS;
 constexpr int NTHREADS = 64 + EPI_THREADS;
 constexpr int STAGE_WARPS = 8;  // epilogue warpgroups 0 and 1 move accumulators out of TMEM
 constexpr long long WAIT_CYCLES = 4000000000ll;  // about 2 s at the boost clock
+std::atomic<int> g_umma_stall{0};  // tqc_step_inject_stall
 
 enum Kind { K_BF16 = 0, K_BF16X3 = 1, K_TF32 = 2 };
 
@@ -64,6 +66,7 @@ struct UmmaParams {
     int32_t rowmajor;  // staging orientation (pick_staging)
     int32_t gmode;     // gather mode of the write-out (pick_staging)
     int32_t bres;      // B stays resident in shared memory (one k-block, one column tile; deep form)
+    int32_t stall;     // test hook: CTA 0 never issues its first k-block's copies
     EpiParams epi;
     int *err;
 };
@@ -290,7 +293,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tA) : "memory");
             asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tB) : "memory");
             int64_t it = 0;
-            bool ok = true;
+            bool ok = true, skipped0 = false;
             if (bres) {  // the one B tile, loaded once
                 mbar_expect_tx(bfull, C::PLANES * bb);
                 tma_load_op(bsm, &tB, 0, 0, bfull, kblk);
@@ -307,6 +310,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                         ok = false;
                         break;
                     }
+                    if (P.stall && blockIdx.x == 0 && it == 0) {
+                        // test hook: stage 0 never fills, so the MMA issuer's bounded wait gives up
+                        skipped0 = true;
+                        continue;
+                    }
                     uint8_t *sa = stages + s * sbytes;
                     mbar_expect_tx(&full[s], (uint32_t)sbytes);
                     tma_load_op(sa, &tA, kb * bk, rt * BM, &full[s], kblk);
@@ -321,9 +329,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     }
                 }
             }
-            if (!ok) {
+            if (!ok || skipped0) {
                 // drain: wait (bounded) for the copies still in flight in every stage
                 for (int64_t j = it > nst ? it - nst : 0; j < it; ++j) {
+                    if (skipped0 && j == 0) continue;  // never issued
                     long long t0 = clock64();
                     while (!mbar_try_wait(&full[j % nst], (uint32_t)((j / nst) & 1)) && clock64() - t0 < WAIT_CYCLES) {
                     }
@@ -709,6 +718,7 @@ cudaError_t launch_kind(const StepArgs &a, int *d_err, cudaStream_t s) {
     p.rowmajor = pk.rowmajor;
     p.gmode = pk.gmode;
     p.err = d_err;
+    p.stall = g_umma_stall.load(std::memory_order_relaxed);
     const int64_t grid = std::min<int64_t>(p.n_units, sm_count());
     umma_step_kernel<BN, KIND, DEEP><<<(unsigned)grid, NTHREADS, C::SMEM, s>>>(tA, tB, tAl, tBl, p);
     return cudaGetLastError();
@@ -766,3 +776,8 @@ cudaError_t launch_umma_step(int cfg, int prec, const StepArgs &a, int *d_err, c
 }
 
 }  // namespace tqc
+
+extern "C" tqc_status tqc_step_inject_stall(int32_t enable) {
+    tqc::g_umma_stall.store(enable ? 1 : 0, std::memory_order_relaxed);
+    return TQC_OK;
+}

@@ -32,7 +32,7 @@ EXPORTS = ["tqc_network_create", "tqc_network_upload", "tqc_destroy", "tqc_plan_
            "tqc_contract_noalloc", "tqc_noalloc_scratch_bytes", "tqc_costmodel_create", "tqc_costmodel_destroy",
            "tqc_costmodel_params", "tqc_costmodel_set_params", "tqc_costmodel_grad", "tqc_costmodel_train",
            "tqc_costmodel_predict", "tqc_costmodel_save", "tqc_costmodel_load", "tqc_plan_features",
-           "tqc_plan_candidates", "tqc_batch_status", "tqc_batch_inject_stall", "tqc_hss_norms", "tqc_hss_select",
+           "tqc_plan_candidates", "tqc_batch_status", "tqc_batch_inject_stall", "tqc_step_inject_stall", "tqc_hss_norms", "tqc_hss_select",
            "tqc_network_select"]
 PLAN_FEATURES = 32
 
@@ -105,6 +105,8 @@ def lib():
         L.tqc_plan_candidates.argtypes = [vp, ctypes.POINTER(PlanOpts), i32, vp, i32p]
         L.tqc_batch_status.argtypes = [vp]
         L.tqc_batch_inject_stall.argtypes = [i32]
+        L.tqc_step_inject_stall.argtypes = [i32]
+        L.tqc_step_inject_stall.restype = ctypes.c_int
         L.tqc_hss_norms.argtypes = [vp, i32, vp, vp]
         L.tqc_hss_select.argtypes = [vp, ctypes.c_int64, vp, vp, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]
         L.tqc_network_select.argtypes = [vp, vp, vp, ctypes.POINTER(vp)]
@@ -465,3 +467,9 @@ def batch_status(stream=None):
 def batch_inject_stall(enable: bool):
     """Fault-injection hook: batched launches carry an item whose wait can never be met."""
     _check(lib().tqc_batch_inject_stall(int(enable)))
+
+
+def step_inject_stall(enable: bool):
+    """Fault-injection hook: tensor-core step launches whose first CTA never
+    fills its first stage, so a bounded wait gives up (see tqc_step_inject_stall)."""
+    _check(lib().tqc_step_inject_stall(int(enable)))

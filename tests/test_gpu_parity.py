@@ -1,7 +1,8 @@
 """CUDA path vs the FP64 oracle, element by element, through the C ABI.
 
-Tolerances: FP32 form <= 1e-5 absolute per
-probability; tensor-core forms <= 1e-3 total variation.  Both are also
+Tolerances: the FP32 and split-BF16 forms <= 1e-5 absolute per probability
+(and 1e-4 of the largest); TF32 <= 1e-3 total variation; plain BF16, which
+misses that gate, only within the bound of its arithmetic (check_tc).  Both are also
 checked relative to the largest probability, since probabilities are ~2^-n.
 All sizes are powers of two (dimension 2 outputs, dimension 4 cuts), so the
 "ragged" cases are tiles wider than the operand (M, N or K below the tile),
@@ -397,13 +398,14 @@ def abs_mass(net):
 
 
 def check_tc(prec, got, net, d, want=None):
-    """TF32 must meet the 1e-3 total-variation gate.  BF16 is checked
-    against the bound its arithmetic gives: every step rounds its two
-    operands to 8 significant bits (unit roundoff 2^-8), so each term of
-    each probability carries a relative error below 2 * n_steps * 2^-8 and
-    TV <= n_steps * 2^-8 * sum_x sum_e |terms|.  (On these pseudo-physical
-    inputs plain BF16 lands near 1.2e-3 to 1.6e-3, above the 1e-3 gate,
-    which is why the library's automatic choice is split BF16.)"""
+    """TF32 must meet the 1e-3 total-variation gate of the tensor-core
+    forms.  Plain BF16 does NOT meet that gate on these pseudo-physical
+    inputs (it lands near 1.2e-3 to 1.6e-3; include/tqc.h says so and the
+    automatic choice never takes it), so it is tested only as what it is: a
+    form whose error stays within the bound its arithmetic gives.  Every
+    step rounds its two operands to 8 significant bits (unit roundoff
+    2^-8), so each term of each probability carries a relative error below
+    2 * n_steps * 2^-8 and TV <= n_steps * 2^-8 * sum_x sum_e |terms|."""
     if want is None:
         want = oracle.recon_bin(net)
     if prec == "tf32":
@@ -480,6 +482,32 @@ def test_autotuned_plan_matches(prec):
     p.contract(out)
     d = p.describe()
     assert d["tuned"] == 1
+    check_fp32(out.cpu().numpy().astype(np.float64), want)
+    p.close()
+    h.close()
+
+
+def test_step_timeout_is_reported_once():
+    """A tensor-core step whose bounded wait gives up (test hook) sets the
+    plan's error word; a call with z_out reports it as TQC_ERR_TIMEOUT and
+    clears it, so the next call is clean and correct."""
+    net = chain3(1250, 0)
+    want = oracle.recon_bin(net) / oracle.total_mass(net)
+    h = tqc.Network(net)
+    p = tqc.Plan(h, precision="bf16x3")
+    assert "tcgen05" in [s_["class"] for s_ in p.describe()["steps"]]
+    out = torch.empty(p.out_elems, dtype=torch.float32, device="cuda")
+    p.contract(out)
+    tqc.step_inject_stall(True)
+    try:
+        p.contract(out)                       # z_out NULL: nothing reported yet
+    finally:
+        tqc.step_inject_stall(False)
+    torch.cuda.synchronize()
+    with pytest.raises(tqc.TqcError) as ei:
+        p.contract(out, want_z=True)          # reports the earlier call's timeout
+    assert ei.value.status == tqc.ERR_TIMEOUT
+    p.contract(out, want_z=True)              # cleared: clean
     check_fp32(out.cpu().numpy().astype(np.float64), want)
     p.close()
     h.close()
