@@ -70,7 +70,9 @@ enum {
                             inputs (measured 1.2e-3 to 1.6e-3: operands keep 8 significant bits);
                             offered for speed comparisons, never chosen by TQC_PREC_AUTO */
     TQC_PREC_BF16X3 = 3, /* dense steps on tcgen05, split BF16 (hi*hi + hi*lo + lo*hi), FP32 accumulate */
-    TQC_PREC_AUTO = 4    /* library's choice (currently BF16X3) */
+    TQC_PREC_AUTO = 4    /* library's choice, per step: TF32 for a step that split BF16 would leave
+                            bound by the tensor pipe (its MMA time above its HBM time), split BF16
+                            for every other tensor-core step; CUDA-core steps stay FP32 */
 };
 
 /* contraction-order search (§III-E-1) */
@@ -214,6 +216,30 @@ TQC_API int32_t tqc_plan_describe(tqc_plan_t plan, char *buf, int32_t size);
  */
 TQC_API tqc_status tqc_contract(tqc_plan_t plan, const uint8_t *fixed_bits, void *d_out, int32_t out_dtype,
                                 double *z_out, void *cuda_stream);
+
+/*
+ * Arbitrary output states (§VII-C measures the reconstruction of a list of
+ * one million arbitrary states): P(x) for each of n_states states, each an
+ * n_qubits-bit integer (qubit q = bit q; n_qubits <= 64), scaled like
+ * tqc_contract (2^{-|E|} / Z, or 2^{-|E|} with TQC_FLAG_NO_RENORM).
+ *   plan     : made with an empty free set (use_free_mask = 1, both masks 0)
+ *              and unsliced; its order and layouts serve every state
+ *   states   : host array of n_states uint64_t, copied to the device each
+ *              call (TQC_ERR_INVALID if a state has bits at or above n_qubits)
+ *   d_out    : caller-owned device buffer, n_states elements of out_dtype
+ *   z_out    : as in tqc_contract
+ * Two forms, reported by tqc_plan_describe as "states_form": "fused" (one
+ * kernel: a CTA contracts one state at a time in shared memory from per-node
+ * tables T_j transposed to [x][cuts], built once per tensor version, FP32
+ * arithmetic) when every single-state intermediate fits in shared memory;
+ * "per-state" otherwise (the plan runs once per state through the ordinary
+ * step kernels, with the state's bits as fixed bits; a host loop).  The
+ * first call allocates the tables and a device copy of the list (grown when a
+ * longer list comes); the list copy and the per-state loop make the call
+ * synchronous with respect to the host.
+ */
+TQC_API tqc_status tqc_contract_states(tqc_plan_t plan, const uint64_t *states, int64_t n_states, void *d_out,
+                                       int32_t out_dtype, double *z_out, void *cuda_stream);
 
 /*
  * End-to-end form with host buffers: copies every subcircuit tensor from

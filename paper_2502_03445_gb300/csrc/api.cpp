@@ -234,6 +234,19 @@ tqc_status tqc_contract(tqc_plan_t plan, const uint8_t *fixed_bits, void *d_out,
     return exec_contract(&plan->p, fixed_bits, d_out, out_dtype, z_out, stream);
 }
 
+tqc_status tqc_contract_states(tqc_plan_t plan, const uint64_t *states, int64_t n_states, void *d_out,
+                               int32_t out_dtype, double *z_out, void *stream) {
+    if (!plan) return fail(TQC_ERR_INVALID, "NULL plan");
+    if (n_states > 0 && (!states || !d_out)) return fail(TQC_ERR_INVALID, "NULL states or d_out");
+    if (out_dtype != TQC_F32 && out_dtype != TQC_F64) return fail(TQC_ERR_INVALID, "out_dtype must be TQC_F32 or TQC_F64");
+    if (!plan->p.net->has_data) return fail(TQC_ERR_INVALID, "shape-only network cannot be contracted");
+    try {
+        return exec_contract_states(&plan->p, states, n_states, d_out, out_dtype, z_out, stream);
+    } catch (const std::bad_alloc &) {
+        return fail(TQC_ERR_OOM, "host allocation failed");
+    }
+}
+
 tqc_status tqc_contract_host(tqc_plan_t plan, const void *const *host_tensors, int32_t in_dtype, void *host_out,
                              int32_t out_dtype, double *z_out, void *stream) {
     if (!plan || !host_out) return fail(TQC_ERR_INVALID, "NULL argument");

@@ -277,6 +277,9 @@ tqc_status update_ksplit(Plan *p) {
     return TQC_OK;
 }
 
+int exec_src_pos_qubit(const Node &nd, int q) { return src_pos_qubit(nd, q); }
+int exec_src_pos_cut(const Node &nd, int c) { return src_pos_cut(nd, c); }
+
 IngestArgs exec_leaf_args(const Plan &p, const TensorPlan &t, int j, const uint8_t *fixed) {
     return leaf_args(p, t, j, fixed, 0, false);
 }
@@ -427,10 +430,42 @@ void exec_release(Plan *p) {
     if (p->d_zws) cudaFree(p->d_zws);
     if (p->d_zinfo) cudaFree(p->d_zinfo);
     if (p->d_kpart) cudaFree(p->d_kpart);
+    if (p->d_tab) cudaFree(p->d_tab);
+    if (p->d_states) cudaFree(p->d_states);
+    p->d_tab = p->d_states = nullptr;
+    p->tab_bytes = p->states_bytes = 0;
+    p->tab_version = 0;
     p->d_ws = p->d_zws = p->d_kpart = nullptr;
     p->kpart_bytes = 0;
     p->d_zinfo = nullptr;
     p->ready = false;
+}
+
+// Total mass Z of the network (every output summed: a scalar network per
+// slice, FP64), then zinfo = [Z, scale = 2^{-|E|} / Z (or 2^{-|E|} without
+// renormalisation)].
+tqc_status exec_total_mass(const Plan &pl, const ExecCtx &c, void *stream) {
+    const Plan *p = &pl;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t ns = p->n_slices();
+    double *zslice = (double *)ws_ptr(c.zws, p->zws_bytes);
+    for (int64_t sl = 0; sl < ns; ++sl) {
+        for (int j = 0; j < p->m; ++j) {
+            const TensorPlan &t = p->ztensors[j];
+            IngestArgs g = leaf_args(*p, t, j, p->fixed_bits.data(), sl, true, &c);
+            g.dst = p->m == 1 ? (void *)(zslice + sl) : (void *)ws_ptr(c.zws, t.offset);
+            TQC_CUDA(launch_ingest(g, (int64_t)1 << t.nbits(), s), "total-mass ingest");
+        }
+        for (size_t i = 0; i < p->zsteps.size(); ++i) {
+            const StepPlan &zs = p->zsteps[i];
+            StepArgs a = step_args(*p, p->ztensors, zs, c.zws, simt_f64_tile());
+            a.epi.mode = EPI_Z;
+            a.epi.out = zs.final ? (void *)(zslice + sl) : (void *)ws_ptr(c.zws, p->ztensors[zs.c].offset);
+            TQC_CUDA(launch_simt_step_f64(a, s), "total-mass step");
+        }
+    }
+    TQC_CUDA(launch_zfinal(zslice, (int)ns, p->net->n_cuts, !(p->flags & TQC_FLAG_NO_RENORM), c.zinfo, s), "zfinal");
+    return TQC_OK;
 }
 
 // The launch sequence of one contract.  Everything it reads and writes
@@ -446,8 +481,6 @@ tqc_status exec_run(Plan &pl, const ExecCtx &c, const uint8_t *fixed_bits, void 
         for (int q = 0; q < p->net->n_qubits; ++q)
             if (fixed_bits[q] > 1) return fail(TQC_ERR_INVALID, "fixed_bits entries must be 0 or 1");
     const int64_t ns = p->n_slices();
-    const int nE = p->net->n_cuts;
-    double *zslice = (double *)ws_ptr(c.zws, p->zws_bytes);
     // a step's tile: the plan's (autotuned or default), or the default and unsplit
     auto step_of = [&](const StepPlan &sp) {
         StepPlan x = sp;
@@ -462,22 +495,8 @@ tqc_status exec_run(Plan &pl, const ExecCtx &c, const uint8_t *fixed_bits, void 
     // on the tensors only, so the allocating path recomputes it only when they
     // changed since the plan last computed it.
     if (c.compute_z) {
-        for (int64_t sl = 0; sl < ns; ++sl) {
-            for (int j = 0; j < p->m; ++j) {
-                const TensorPlan &t = p->ztensors[j];
-                IngestArgs g = leaf_args(*p, t, j, fixed, sl, true, &c);
-                g.dst = p->m == 1 ? (void *)(zslice + sl) : (void *)ws_ptr(c.zws, t.offset);
-                TQC_CUDA(launch_ingest(g, (int64_t)1 << t.nbits(), s), "total-mass ingest");
-            }
-            for (size_t i = 0; i < p->zsteps.size(); ++i) {
-                const StepPlan &zs = p->zsteps[i];
-                StepArgs a = step_args(*p, p->ztensors, zs, c.zws, simt_f64_tile());
-                a.epi.mode = EPI_Z;
-                a.epi.out = zs.final ? (void *)(zslice + sl) : (void *)ws_ptr(c.zws, p->ztensors[zs.c].offset);
-                TQC_CUDA(launch_simt_step_f64(a, s), "total-mass step");
-            }
-        }
-        TQC_CUDA(launch_zfinal(zslice, (int)ns, nE, !(p->flags & TQC_FLAG_NO_RENORM), c.zinfo, s), "zfinal");
+        st = exec_total_mass(*p, c, stream);
+        if (st != TQC_OK) return st;
         if (z_computed) *z_computed = true;
     }
 

@@ -90,6 +90,23 @@ int in_bytes_of(int klass, int prec) {
 
 }  // namespace
 
+// Operand type of one tensor-core step.  A given precision applies to every
+// step; under TQC_PREC_AUTO each step takes TF32 when split BF16 would leave
+// it bound by the tensor pipe (its three MMAs per product take longer than
+// moving its algorithmic HBM bytes), where TF32's single MMA per product at
+// half the BF16 rate is 1.5x faster; every other step keeps split BF16: an
+// HBM-bound step gains nothing from TF32 (both store 4 bytes per element)
+// and split BF16 is the more accurate (operands exact to about 2^-16
+// relative, against 2^-11 for TF32).
+int step_prec(int prec, int mb, int nb, int kb) {
+    if (prec != TQC_PREC_AUTO) return prec;
+    const CostConsts cc;
+    const double macs = std::ldexp(1.0, mb + nb + kb);
+    const double bytes = 4.0 * (std::ldexp(1.0, mb + kb) + std::ldexp(1.0, nb + kb)) + 4.0 * std::ldexp(1.0, mb + nb);
+    const double t_split_bf16 = 2.0 * macs * 3.0 / cc.bf16_fps;
+    return t_split_bf16 > bytes / cc.hbm_Bps ? TQC_PREC_TF32 : TQC_PREC_BF16X3;
+}
+
 int choose_class(int mb, int nb, int kb, int prec) {
     if (prec == TQC_PREC_FP32) return KC_SIMT;
     // tensor cores only where the step is a real contraction: K >= 64 and a
@@ -100,6 +117,7 @@ int choose_class(int mb, int nb, int kb, int prec) {
 
 StepCost step_cost(int mb, int nb, int kb, int klass, int prec, const CostConsts &cc) {
     StepCost c;
+    prec = step_prec(prec, mb, nb, kb);
     c.macs = std::ldexp(1.0, mb + nb + kb);
     int ib = in_bytes_of(klass, prec);
     c.bytes = ib * (std::ldexp(1.0, mb + kb) + std::ldexp(1.0, nb + kb)) + 4.0 * std::ldexp(1.0, mb + nb);
@@ -116,7 +134,9 @@ StepCost step_cost(int mb, int nb, int kb, int klass, int prec, const CostConsts
 
 namespace {
 
-int effective_prec(int prec) { return prec == TQC_PREC_AUTO ? TQC_PREC_BF16X3 : prec; }
+// The plan-level precision: TQC_PREC_AUTO stays AUTO and is resolved per
+// step by step_prec.
+int effective_prec(int prec) { return prec; }
 
 // Step cost under one of three objectives: 0 = predicted time (default),
 // 1 = multiply-adds only (the paper's cost unit), 2 = HBM bytes only.
@@ -346,7 +366,7 @@ Built build_steps(const Plan &p, const NetBits &nb, const std::vector<std::array
         }
         st.kb = 2 * popc(shared);
         st.c = (int)B.t.size() - 1;
-        st.prec = zplan ? TQC_PREC_FP32 : prec;
+        st.prec = zplan ? TQC_PREC_FP32 : step_prec(prec, st.mb, st.nb, st.kb);
         st.klass = zplan ? KC_SIMT : choose_class(st.mb, st.nb, st.kb, prec);
         st.final = (s + 1 == pairs.size());
         B.s.push_back(st);
@@ -554,10 +574,16 @@ std::vector<double> plan_features(const Plan &p) {
     f[k++] = small_k;
     f[k++] = (double)p.free_qubits.size();
     f[k++] = lg(pred * 1e9);
-    f[k++] = (double)(p.precision == TQC_PREC_BF16);
-    f[k++] = (double)(p.precision == TQC_PREC_BF16X3);
-    f[k++] = (double)(p.precision == TQC_PREC_TF32);
-    f[k++] = (double)(p.precision == TQC_PREC_FP32);
+    // operand types: the share of the tensor-core steps in each (the plain
+    // FP32 form has none)
+    double n_prec[4] = {0, 0, 0, 0};  // BF16, BF16X3, TF32, FP32
+    for (auto &st : p.steps) {
+        if (st.klass != KC_UMMA) continue;
+        n_prec[st.prec == TQC_PREC_BF16 ? 0 : st.prec == TQC_PREC_BF16X3 ? 1 : 2] += 1;
+    }
+    n_prec[3] = p.precision == TQC_PREC_FP32 ? 1.0 : 0.0;
+    for (int i = 0; i < 3; ++i) f[k++] = n_umma > 0 ? n_prec[i] / n_umma : 0.0;
+    f[k++] = n_prec[3];
     f[k++] = (double)p.m;
     f[k++] = (double)p.net->n_cuts;
     f[k++] = lg(p.ws_bytes);
@@ -849,6 +875,10 @@ std::string plan_describe(const Plan &pl) {
         if (p->n_slices() > 1) launches += 1;
     }
     os << "],\"launches_per_contract\":" << launches << ",\"total_mass_launches\":" << z_launches;
+    // how tqc_contract_states runs this plan (plans with no free qubits only)
+    const char *sf = "none";
+    if (p->free_qubits.empty()) sf = states_fused_floats(*p) >= 0 ? "fused" : "per-state";
+    os << ",\"states_form\":\"" << sf << "\"";
     char buf[256];
     std::snprintf(buf, sizeof buf, ",\"flops\":%.6g,\"bytes\":%.6g,\"predicted_s\":%.6g,\"ws_bytes\":%lld}", p->flops,
                   p->bytes, p->predicted_s, (long long)p->ws_bytes);

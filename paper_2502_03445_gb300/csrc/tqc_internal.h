@@ -151,6 +151,12 @@ struct Plan {
     int tuned = 0;
     int profile = 0;
     uint64_t z_version = 0;                // network version the cached Z belongs to
+    void *d_tab = nullptr;                 // state lists: per-node tables Tt_j[x][cuts] (FP32)
+    int64_t tab_bytes = 0;
+    std::vector<int64_t> tab_off;
+    uint64_t tab_version = 0;              // network version the tables belong to
+    void *d_states = nullptr;              // state lists: the last list, on the device
+    int64_t states_bytes = 0;
     std::vector<std::vector<std::array<void *, 2>>> step_events;  // per step: (start, stop) cudaEvent_t
     int64_t n_slices() const { return (int64_t)1 << (2 * sliced.size()); }
     int64_t out_elems() const { return (int64_t)1 << free_qubits.size(); }
@@ -169,6 +175,7 @@ int costmodel_n_in(::tqc_costmodel *cm);
 StepCost step_cost(int mb, int nb, int kb, int klass, int prec, const CostConsts &cc);
 std::vector<double> plan_features(const Plan &p);   // learned cost-model features
 int choose_class(int mb, int nb, int kb, int prec);
+int step_prec(int prec, int mb, int nb, int kb);  // per-step operand type (resolves TQC_PREC_AUTO)
 
 // Where one contract reads and writes.  The allocating path uses the
 // plan's own device state; the allocation-free entry point points every
@@ -192,6 +199,17 @@ tqc_status exec_prepare(Plan *p);
 // synchronisation).  *z_computed tells whether the total mass was computed.
 tqc_status exec_run(Plan &p, const ExecCtx &c, const uint8_t *fixed_bits, void *d_out, int out_dtype,
                     void *stream, bool *z_computed);
+// Arbitrary state list (states.cu): P(x) of n states on a plan with no free qubits.
+tqc_status exec_contract_states(Plan *p, const uint64_t *states, int64_t n, void *d_out, int out_dtype,
+                                double *z_out, void *stream);
+// Shared-memory floats of the fused state-list kernel for a plan, or -1 when
+// the plan's states run one at a time through the ordinary step kernels.
+int states_fused_floats(const Plan &p);
+// Total mass Z into c.zinfo (and the output scale), stream-ordered.
+tqc_status exec_total_mass(const Plan &p, const ExecCtx &c, void *stream);
+// Device source bit positions of a node tensor: output qubit q, cut c (-1 if absent).
+int exec_src_pos_qubit(const Node &nd, int q);
+int exec_src_pos_cut(const Node &nd, int c);
 tqc_status exec_contract(Plan *p, const uint8_t *fixed_bits, void *d_out, int out_dtype, double *z_out,
                          void *stream);
 void exec_release(Plan *p);

@@ -27,7 +27,8 @@ PREC_NAMES = {"fp32": PREC_FP32, "tf32": PREC_TF32, "bf16": PREC_BF16, "bf16x3":
 
 # every symbol include/tqc.h declares
 EXPORTS = ["tqc_network_create", "tqc_network_upload", "tqc_destroy", "tqc_plan_opts_default", "tqc_plan",
-           "tqc_plan_info", "tqc_plan_step", "tqc_plan_describe", "tqc_contract", "tqc_contract_host",
+           "tqc_plan_info", "tqc_plan_step", "tqc_plan_describe", "tqc_contract", "tqc_contract_states",
+           "tqc_contract_host",
            "tqc_contract_batch", "tqc_plan_profile", "tqc_plan_step_time", "tqc_plan_destroy", "tqc_last_error",
            "tqc_contract_noalloc", "tqc_noalloc_scratch_bytes", "tqc_costmodel_create", "tqc_costmodel_destroy",
            "tqc_costmodel_params", "tqc_costmodel_set_params", "tqc_costmodel_grad", "tqc_costmodel_train",
@@ -82,6 +83,8 @@ def lib():
         L.tqc_plan_describe.restype = i32
         L.tqc_contract.argtypes = [vp, u8p, vp, i32, ctypes.POINTER(ctypes.c_double), vp]
         L.tqc_contract_host.argtypes = [vp, vp, i32, vp, i32, ctypes.POINTER(ctypes.c_double), vp]
+        L.tqc_contract_states.argtypes = [vp, vp, ctypes.c_int64, vp, i32, ctypes.POINTER(ctypes.c_double), vp]
+        L.tqc_contract_states.restype = ctypes.c_int
         L.tqc_contract_batch.argtypes = [vp, vp, i32, vp]
         L.tqc_plan_destroy.argtypes = [vp]
         L.tqc_plan_profile.argtypes = [vp, i32]
@@ -309,6 +312,22 @@ class Plan:
         z = ctypes.c_double()
         _check(lib().tqc_contract(self.handle, None if fb is None else fb.ctypes.data, out.data_ptr(), dt,
                                   ctypes.byref(z) if want_z else None, _stream_ptr(stream)))
+        return z.value if want_z else None
+
+    def contract_states(self, states, out, want_z=False, stream=None):
+        """P of each state in ``states`` (ints, or a uint64 array; qubit q =
+        bit q) into ``out`` (CUDA float32/float64 tensor of len(states)).
+        The plan must have no free qubits (``free_qubits=[]``)."""
+        import torch
+        st = np.ascontiguousarray(np.asarray(states, dtype=np.uint64))
+        assert out.is_cuda and out.is_contiguous() and out.numel() == len(st)
+        if out.dtype not in (torch.float32, torch.float64):
+            raise TypeError("out must be float32 or float64")
+        dt = F64 if out.dtype == torch.float64 else F32
+        z = ctypes.c_double()
+        _check(lib().tqc_contract_states(self.handle, st.ctypes.data if len(st) else None, len(st),
+                                         out.data_ptr() if len(st) else None, dt,
+                                         ctypes.byref(z) if want_z else None, _stream_ptr(stream)))
         return z.value if want_z else None
 
     def contract_host(self, host_tensors, host_out, in_dtype=F64, stream=None):

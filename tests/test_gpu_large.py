@@ -170,7 +170,9 @@ def test_grid64_bin_stream():
 def test_grid30_full_vector(prec):
     """bench.py's workload and launch configuration: every qubit free, the
     default plan (tensor-core steps with the direct and staged epilogues, or
-    the plain FP32 form), renormalised FP32 output.  All 2^30 outputs are
+    the plain FP32 form), renormalised FP32 output.  Gates: 1e-5 absolute
+    everywhere; 1e-4 of the largest probability for FP32-class forms, total
+    variation 1e-3 when a step runs in TF32.  All 2^30 outputs are
     compared with oracle C, a quarter at a time (qubits 28 and 29 fixed), and
     256 uniformly drawn ones with oracle A."""
     net = workloads.grid30(0)
@@ -180,8 +182,9 @@ def test_grid30_full_vector(prec):
     z = p.contract(out, want_z=True)
     torch.cuda.synchronize()
     d = p.describe()
+    tf32 = any(s_["class"] == "tcgen05" and s_["prec"] == "tf32" for s_ in d["steps"])
     if prec == "auto":
-        assert [s_["class"] for s_ in d["steps"]] == ["tcgen05"] * 3
+        assert d["steps"][-1]["class"] == "tcgen05" and d["steps"][-1]["prec"] == "bf16x3", d["steps"]
     z_or = oracle.total_mass(net)
     assert abs(z - z_or) <= 1e-9
     got = out.cpu().numpy()
@@ -208,8 +211,10 @@ def test_grid30_full_vector(prec):
     tv = 0.5 * err_sum / abs_sum
     print(f"grid30/{prec}: tiles {[s_['tile'] for s_ in d['steps']]} full vector: max|err| {max_err:.3e} "
           f"max|P| {max_p:.3e} (err/max {max_err / max_p:.2e}) TV {tv:.3e}; oracle A sample max|err| {err_a:.3e}")
-    assert err_a <= FP32_ATOL and err_a <= 1e-4 * max_p
-    assert max_err <= FP32_ATOL
-    assert max_err <= 1e-4 * max_p
+    assert err_a <= FP32_ATOL and max_err <= FP32_ATOL
+    if tf32:        # a TF32 step: the total-variation gate of the tensor-core forms
+        assert tv <= TC_TV, tv
+    else:           # FP32-class arithmetic: also within 1e-4 of the largest probability
+        assert err_a <= 1e-4 * max_p and max_err <= 1e-4 * max_p
     p.close()
     h.close()

@@ -181,3 +181,51 @@ def test_k_blocked_layout_rule(prec, cuts, expect):
     assert cuts_a == cuts_b
     p.close()
     h.close()
+
+
+def test_auto_precision_is_chosen_per_step():
+    """TQC_PREC_AUTO: TF32 for a step that split BF16 would leave bound by
+    the tensor pipe, split BF16 for HBM-bound tensor-core steps (grid30's
+    final step writes 4.3 GB for 5.5e11 flops), FP32 on CUDA cores."""
+    # deep K: M = 2^11, N = 2^10, K = 4^7 -- 69 GFLOP per 210 MB
+    deep = tqc.Network(shape_net(21, [(0, 1)] * 7, [list(range(11)), list(range(11, 21))]), shape_only=True)
+    p = tqc.Plan(deep)
+    d = p.describe()
+    assert d["precision"] == "auto"
+    assert [(s["class"], s["prec"], s["log2_k"]) for s in d["steps"]] == [("tcgen05", "tf32", 14)]
+    assert p.step(0)["precision"] == tqc.PREC_TF32
+    p.close(), deep.close()
+    g30 = tqc.Network(workloads.grid30(), shape_only=True)
+    p = tqc.Plan(g30)
+    d = p.describe()
+    last = d["steps"][-1]
+    assert last["class"] == "tcgen05" and last["prec"] == "bf16x3", d["steps"]
+    assert last["log2_m"] + last["log2_n"] == 30
+    for s in d["steps"]:
+        if s["class"] == "tcgen05":
+            m, n, k = 2 ** s["log2_m"], 2 ** s["log2_n"], 2 ** s["log2_k"]
+            bound = 2 * m * n * k * 3 / 1.6e15 > 4 * (m * k + n * k + m * n) / 6.79e12
+            assert s["prec"] == ("tf32" if bound else "bf16x3"), s
+    # a forced precision applies to every tensor-core step
+    for prec in ("bf16x3", "tf32"):
+        pf = tqc.Plan(g30, precision=prec)
+        assert {s["prec"] for s in pf.describe()["steps"] if s["class"] == "tcgen05"} == {prec}
+        pf.close()
+    p.close(), g30.close()
+
+
+def test_auto_precision_on_the_tensor_bound_bins():
+    """The 48-qubit QAOA and 64-qubit grid bins (32 GB budget): AUTO runs
+    their tensor-bound steps in TF32, the rest in split BF16."""
+    for net in (workloads.qaoa48(0), workloads.grid64_bin(0, 0)):
+        h = tqc.Network(net, shape_only=True)
+        p = tqc.Plan(h, mem_budget=32 << 30)
+        steps = p.describe()["steps"]
+        tc = [s for s in steps if s["class"] == "tcgen05"]
+        assert steps[-1]["prec"] == "tf32", steps
+        assert {s["prec"] for s in tc} == {"tf32", "bf16x3"}, steps
+        for s in tc:
+            m, n, k = 2 ** s["log2_m"], 2 ** s["log2_n"], 2 ** s["log2_k"]
+            bound = 2 * m * n * k * 3 / 1.6e15 > 4 * (m * k + n * k + m * n) / 6.79e12
+            assert s["prec"] == ("tf32" if bound else "bf16x3"), s
+        p.close(), h.close()
