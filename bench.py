@@ -64,7 +64,7 @@ def parse():
     ap.add_argument("--batch", type=int, default=0,
                     help="instead: time the batched persistent launch over this many networks")
     ap.add_argument("--batch-n-lo", type=int, default=16)
-    ap.add_argument("--batch-n-hi", type=int, default=24)
+    ap.add_argument("--batch-n-hi", type=int, default=28)
     ap.add_argument("--workload", default="grid30", choices=["grid30", "qaoa48", "grid64"],
                     help="qaoa48 / grid64: time one bin of 2^24 states of the tensor-bound networks instead")
     ap.add_argument("--mem-budget-gb", type=float, default=32.0,
