@@ -87,7 +87,8 @@ enum {
 
 /* plan flags */
 enum {
-    TQC_FLAG_NO_RENORM = 1       /* skip division by the total mass Z (Z still reported) */
+    TQC_FLAG_NO_RENORM = 1,      /* skip division by the total mass Z (Z still reported) */
+    TQC_FLAG_NO_REUSE = 2        /* recompute every intermediate on every tqc_contract (see there) */
 };
 
 /*
@@ -208,6 +209,14 @@ TQC_API int32_t tqc_plan_describe(tqc_plan_t plan, char *buf, int32_t size);
  * Steps: bin restriction and layout (ingest), the pairwise contractions,
  * FP64 sum over slices, renormalisation by Z.  The first call allocates the
  * plan's workspace.
+ * Reuse across bins: the plan's workspace keeps every leaf operand and
+ * intermediate of the previous call.  A call whose bin differs only in the
+ * fixed bits of some subcircuits (same tensors, same free set) re-ingests
+ * only those subcircuits' leaves and recomputes only the steps that depend
+ * on them (not for slice-dependent tensors, which the slice loop rewrites);
+ * the last step always runs.  tqc_plan_describe reports what the last call
+ * kept; TQC_FLAG_NO_REUSE turns it off, and so does passing the plan to
+ * tqc_contract_batch (its launches rewrite the workspace).
  * Device-side failures: every wait of a tensor-core step is bounded; one that
  * gives up sets the plan's error word and its output is wrong.  The word is
  * read only by a call with a non-NULL z_out: that call returns
@@ -412,6 +421,76 @@ TQC_API tqc_status tqc_hss_select(tqc_net_t net, int64_t s_max, int32_t *counts,
  * the source network's total mass to get the product states' probabilities;
  * padded entries are zero.  Destroy with tqc_destroy. */
 TQC_API tqc_status tqc_network_select(tqc_net_t net, const int32_t *counts, const int32_t *states, tqc_net_t *out);
+
+/*
+ * Cut finder (§VI): Greedy Graph Growing (Alg. 2) over the circuit's
+ * two-qubit gates, merging the partitions joined by the edge of least
+ * merging cost (Alg. 3, Table I) until none is valid; one-qubit gates then
+ * join an adjacent two-qubit gate.  Among the partitions found for
+ * thresholds K_t = 1..k_sweep_max (or the one given) it returns the one of
+ * least T = T_QPU + T_classical (Eq. cut_objective): T_QPU by Eq.
+ * qpu_runtime, T_classical the planner's estimated time to contract the
+ * resulting network for the bin of the lowest cost_free_qubits qubits (the
+ * analytic step-time model, times exp of the learned cost model's output
+ * when costmodel_path is given, in place of Eq. classical_runtime's FLOP
+ * count over FLOP/s).  Host only (the learned model runs on the device).
+ *   gate_qubits : n_gates x 2 qubit ids in time order; second = -1 for a
+ *                 one-qubit gate
+ *   gate_part   : out, n_gates subcircuit ids (numbered by first gate); a
+ *                 wire is cut wherever consecutive gates on it sit in
+ *                 different subcircuits (upstream end: the earlier gate's);
+ *                 a wire without two-qubit gates joins subcircuit 0, whose
+ *                 width may then exceed w_max (result->max_width says)
+ * Readings of what the paper leaves open: a subcircuit's width is its number
+ * of wire segments (a wire that leaves and re-enters comes back on a new
+ * qubit) and its size its number of two-qubit gates; the contraction edges
+ * of two neighbouring partitions are the distinct cuts touching either;
+ * every merging cost is recomputed after each merge and ties go to the
+ * lowest (earlier gate, later gate) edge; shots = 2^width limited to
+ * [2^shots_log2_min, 2^shots_log2_max]; depth = layers of the subcircuit's
+ * gates scheduled as early as possible.
+ */
+typedef struct {
+    int32_t w_max;            /* most qubits of a subcircuit (hard limit) */
+    int32_t s_max;            /* most two-qubit gates of a subcircuit (hard limit) */
+    int32_t k_t;              /* contraction-edge threshold (soft); <= 0: sweep 1..k_sweep_max */
+    int32_t k_sweep_max;
+    double q_max;             /* merging-cost cutoff; <= 0: none */
+    double t_gate, t_meas;    /* seconds per gate layer and per measurement (Eq. qpu_runtime) */
+    int32_t shots_log2_min, shots_log2_max;
+    int32_t n_qpus;           /* QPUs running subcircuits in parallel (T_QPU is divided by it) */
+    int32_t cost_free_qubits; /* T_classical: the bin of this many lowest qubits (<= 40) */
+    int32_t precision;        /* of the plan estimating T_classical */
+    const char *costmodel_path; /* learned cost model for T_classical, or NULL */
+} tqc_cut_opts;
+
+typedef struct {
+    int32_t n_sub, n_cuts, k_t, max_width;
+    double t_qpu, t_classical, t_total;  /* seconds */
+    double cutqc_mults, tensorqc_mults;  /* per state: brute force 4^|E| (m-1); the plan's order on one state */
+} tqc_cut_result;
+
+/* Defaults: w_max 16, no gate limit, K_t swept 1..16, no Q_max, t_gate 1e-7 s,
+ * t_meas 1e-6 s, shots 2^10..2^20, 10 QPUs (§VII-A), a 2^20-state bin, AUTO. */
+TQC_API void tqc_cut_opts_default(tqc_cut_opts *opts);
+TQC_API tqc_status tqc_find_cuts(int32_t n_qubits, int32_t n_gates, const int32_t *gate_qubits,
+                                 const tqc_cut_opts *opts, int32_t *gate_part, tqc_cut_result *result);
+
+/*
+ * Classical cost of a plan against the brute-force reconstruction (§III-C;
+ * §VIII, Fig. cost_ratio compares CutQC's brute force with TensorQC's
+ * contraction in scalar multiplications).
+ */
+typedef struct {
+    double cutqc_mults_per_state;    /* 4^|E| (m - 1): every cut assignment, m - 1 products each */
+    double tensorqc_mults_per_state; /* the plan's contraction order on a single state */
+    double ratio;                    /* cutqc / tensorqc, per state */
+    double plan_mults;               /* the plan itself: every slice and every state of its bin */
+    double plan_mults_per_state;     /* plan_mults / 2^F (shared work across the bin) */
+    int32_t k_max;                   /* most contraction edges (inner + outer cuts) of a single-state step */
+    double tn_upper_bound;           /* 4^{k_max} m (Eq. tn_upper_bound) */
+} tqc_cost_report;
+TQC_API tqc_status tqc_plan_cost_report(tqc_plan_t plan, tqc_cost_report *out);
 
 TQC_API const char *tqc_last_error(void);
 

@@ -795,6 +795,9 @@ tqc_status tqc_contract_batch(const tqc_plan_t *plans, void *const *d_outs, int3
     for (int i = 0; i < n; ++i)
         if (!plans[i] || !d_outs[i]) return fail(TQC_ERR_INVALID, "NULL plan or output in batch");
     std::lock_guard<std::mutex> lk(g_batch_mu);
+    // the batch (and every replay of a graph that captured it) rewrites these
+    // plans' workspaces: they keep no intermediates across tqc_contract calls
+    for (int i = 0; i < n; ++i) plans[i]->p.batched = true;
     std::vector<const void *> key;
     for (int i = 0; i < n; ++i) {
         key.push_back(plans[i]);

@@ -471,7 +471,7 @@ tqc_status exec_total_mass(const Plan &pl, const ExecCtx &c, void *stream) {
 // The launch sequence of one contract.  Everything it reads and writes
 // besides the caller's output comes from `c`.
 tqc_status exec_run(Plan &pl, const ExecCtx &c, const uint8_t *fixed_bits, void *d_out, int out_dtype, void *stream,
-                    bool *z_computed) {
+                    bool *z_computed, const std::vector<char> *keep) {
     Plan *p = &pl;
     cudaStream_t s = (cudaStream_t)stream;
     tqc_status st = TQC_OK;
@@ -519,6 +519,7 @@ tqc_status exec_run(Plan &pl, const ExecCtx &c, const uint8_t *fixed_bits, void 
         for (int j = 0; j < p->m; ++j) {
             const TensorPlan &t = p->tensors[j];
             if (sl > 0 && !t.slice_dep) continue;
+            if (keep && (*keep)[(size_t)j]) continue;  // still in the workspace from the last call
             IngestArgs g = leaf_args(*p, t, j, fixed, sl, false, &c);
             g.dst = ws_ptr(c.ws, t.offset);
             if (t.storage == ST_BF16X2) g.dst_lo = ws_ptr(c.ws, t.offset + t.plane_bytes);
@@ -528,6 +529,7 @@ tqc_status exec_run(Plan &pl, const ExecCtx &c, const uint8_t *fixed_bits, void 
         for (size_t si = 0; si < p->steps.size(); ++si) {
             const StepPlan sp = step_of(p->steps[si]);
             if (sl > 0 && !p->tensors[sp.c].slice_dep) continue;
+            if (keep && (*keep)[(size_t)sp.c]) continue;
             StepArgs a = step_args(*p, p->tensors, sp, c.ws, tile_of(sp));
             const TensorPlan &tc = p->tensors[sp.c];
             a.epi.zinfo = c.zinfo;
@@ -594,10 +596,38 @@ tqc_status exec_contract(Plan *p, const uint8_t *fixed_bits, void *d_out, int ou
     c.kpart = p->d_kpart;
     c.compute_z = p->z_version != p->net->version;
     c.profile = p->profile != 0;
+    if (fixed_bits)
+        for (int q = 0; q < p->net->n_qubits; ++q)
+            if (fixed_bits[q] > 1) return fail(TQC_ERR_INVALID, "fixed_bits entries must be 0 or 1");
+    // Tensors whose leaves all kept their bin restriction since the last call
+    // (same tensor version) are still valid in the workspace; slice-dependent
+    // ones were overwritten by later slices, and the root is the output.
+    const uint8_t *fixed = fixed_bits ? fixed_bits : p->fixed_bits.data();
+    std::vector<int64_t> keys((size_t)p->m);
+    for (int j = 0; j < p->m; ++j) keys[(size_t)j] = leaf_args(*p, p->tensors[(size_t)j], j, fixed, 0, false).src_base;
+    std::vector<char> keep(p->tensors.size(), 0);
+    p->reused_leaves = p->reused_steps = 0;
+    if (!(p->flags & TQC_FLAG_NO_REUSE) && !p->batched && p->reuse_ok && p->reuse_version == p->net->version &&
+        p->m > 1) {
+        uint64_t dirty = 0;
+        for (int j = 0; j < p->m; ++j)
+            if (keys[(size_t)j] != p->leaf_key[(size_t)j]) dirty |= 1ull << j;
+        for (size_t i = 0; i + 1 < p->tensors.size(); ++i) {
+            const TensorPlan &t = p->tensors[i];
+            if (t.slice_dep || (t.leaves & dirty)) continue;
+            keep[i] = 1;
+            if ((int)i < p->m) ++p->reused_leaves;
+            else ++p->reused_steps;
+        }
+    }
+    p->reuse_ok = false;  // set again once every launch of this call is issued
     bool zc = false;
-    st = exec_run(*p, c, fixed_bits, d_out, out_dtype, stream, &zc);
+    st = exec_run(*p, c, fixed_bits, d_out, out_dtype, stream, &zc, &keep);
     if (st != TQC_OK) return st;
     if (zc) p->z_version = p->net->version;
+    p->leaf_key = keys;
+    p->reuse_version = p->net->version;
+    p->reuse_ok = true;
     if (z_out) {
         // Z, the scale and the error word, which stays set from the call whose
         // bounded wait gave up until a call with z_out reports (and clears) it

@@ -879,6 +879,7 @@ std::string plan_describe(const Plan &pl) {
     const char *sf = "none";
     if (p->free_qubits.empty()) sf = states_fused_floats(*p) >= 0 ? "fused" : "per-state";
     os << ",\"states_form\":\"" << sf << "\"";
+    os << ",\"reused_leaves\":" << p->reused_leaves << ",\"reused_steps\":" << p->reused_steps;
     char buf[256];
     std::snprintf(buf, sizeof buf, ",\"flops\":%.6g,\"bytes\":%.6g,\"predicted_s\":%.6g,\"ws_bytes\":%lld}", p->flops,
                   p->bytes, p->predicted_s, (long long)p->ws_bytes);

@@ -388,6 +388,7 @@ tqc_status exec_contract_states(Plan *p, const uint64_t *states, int64_t n, void
         // per state: the single-state plan with the state's bits as the fixed bits
         std::vector<uint8_t> fixed((size_t)p->net->n_qubits);
         c.compute_z = false;
+        p->reuse_ok = false;  // the workspace now holds other states' intermediates
         for (int64_t i = 0; i < n; ++i) {
             for (int q = 0; q < p->net->n_qubits; ++q) fixed[(size_t)q] = (uint8_t)((states[i] >> q) & 1);
             st = exec_run(*p, c, fixed.data(), (char *)d_out + i * esize, out_dtype, stream, nullptr);

@@ -108,7 +108,7 @@ struct CostConsts {
     double hbm_Bps = 6.79e12;       // measured copy bandwidth of this part
     double simt_fps = 5.0e13;       // sustained FP32 CUDA-core rate of the plain step kernel
     double bf16_fps = 1.6e15;       // sustained BF16 tcgen05 rate
-    double tf32_fps = 0.8e15;
+    double tf32_fps = 0.65e15;      // measured on 128 x 256 tiles at K = 2^10 (655-667 TF/s)
     double launch_s = 3.0e-6;       // per kernel launch / tail
 };
 
@@ -157,6 +157,12 @@ struct Plan {
     uint64_t tab_version = 0;              // network version the tables belong to
     void *d_states = nullptr;              // state lists: the last list, on the device
     int64_t states_bytes = 0;
+    // intermediates kept across calls (bins that differ in some leaves' fixed bits)
+    bool reuse_ok = false;                 // the workspace holds the last call's values
+    bool batched = false;                  // part of a batched launch, whose replays rewrite the workspace
+    uint64_t reuse_version = 0;            // network version of those values
+    std::vector<int64_t> leaf_key;         // per leaf: its bin restriction (source offset) in that call
+    int reused_leaves = 0, reused_steps = 0;  // skipped in the last call
     std::vector<std::vector<std::array<void *, 2>>> step_events;  // per step: (start, stop) cudaEvent_t
     int64_t n_slices() const { return (int64_t)1 << (2 * sliced.size()); }
     int64_t out_elems() const { return (int64_t)1 << free_qubits.size(); }
@@ -198,7 +204,7 @@ tqc_status exec_prepare(Plan *p);
 // The launch sequence of one contract on `stream` (no allocation, no
 // synchronisation).  *z_computed tells whether the total mass was computed.
 tqc_status exec_run(Plan &p, const ExecCtx &c, const uint8_t *fixed_bits, void *d_out, int out_dtype,
-                    void *stream, bool *z_computed);
+                    void *stream, bool *z_computed, const std::vector<char> *keep = nullptr);
 // Arbitrary state list (states.cu): P(x) of n states on a plan with no free qubits.
 tqc_status exec_contract_states(Plan *p, const uint64_t *states, int64_t n, void *d_out, int out_dtype,
                                 double *z_out, void *stream);

@@ -682,7 +682,8 @@ cudaError_t launch_kind(const StepArgs &a, int *d_err, cudaStream_t s) {
     // as many copies are in flight ahead of the tensor pipe.  Not for rows
     // longer than 64 KB: a box then spans many pages, and twice the boxes
     // per byte cost more in address translation than the deeper ring gains.
-    const bool sw64 = DEEP && !a.kblk && K >= ((uint64_t)1 << SW64_MIN_LOG2_K) && K * C::ELEM <= ((uint64_t)1 << 16);
+    const bool sw64 = DEEP && KIND != K_TF32 && !a.kblk && K >= ((uint64_t)1 << SW64_MIN_LOG2_K) &&
+                      K * C::ELEM <= ((uint64_t)1 << 16);
     const uint32_t bk = (sw64 ? 64 : 128) / C::ELEM;
     if (K < (uint64_t)bk) return cudaErrorInvalidValue;
     CUtensorMap tA, tB, tAl, tBl;

@@ -23,6 +23,7 @@ F64, F32 = 0, 1
 PREC_FP32, PREC_TF32, PREC_BF16, PREC_BF16X3, PREC_AUTO = range(5)
 PLANNER_GREEDY, PLANNER_EXHAUSTIVE, PLANNER_LEARNED, PLANNER_AUTO = range(4)
 FLAG_NO_RENORM = 1
+FLAG_NO_REUSE = 2
 PREC_NAMES = {"fp32": PREC_FP32, "tf32": PREC_TF32, "bf16": PREC_BF16, "bf16x3": PREC_BF16X3, "auto": PREC_AUTO}
 
 # every symbol include/tqc.h declares
@@ -34,7 +35,7 @@ EXPORTS = ["tqc_network_create", "tqc_network_upload", "tqc_destroy", "tqc_plan_
            "tqc_costmodel_params", "tqc_costmodel_set_params", "tqc_costmodel_grad", "tqc_costmodel_train",
            "tqc_costmodel_predict", "tqc_costmodel_save", "tqc_costmodel_load", "tqc_plan_features",
            "tqc_plan_candidates", "tqc_batch_status", "tqc_batch_inject_stall", "tqc_step_inject_stall", "tqc_hss_norms", "tqc_hss_select",
-           "tqc_network_select"]
+           "tqc_network_select", "tqc_cut_opts_default", "tqc_find_cuts", "tqc_plan_cost_report"]
 PLAN_FEATURES = 32
 
 
@@ -113,6 +114,12 @@ def lib():
         L.tqc_hss_norms.argtypes = [vp, i32, vp, vp]
         L.tqc_hss_select.argtypes = [vp, ctypes.c_int64, vp, vp, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]
         L.tqc_network_select.argtypes = [vp, vp, vp, ctypes.POINTER(vp)]
+        L.tqc_cut_opts_default.argtypes = [vp]
+        L.tqc_cut_opts_default.restype = None
+        L.tqc_find_cuts.argtypes = [i32, i32, vp, vp, vp, vp]
+        L.tqc_find_cuts.restype = ctypes.c_int
+        L.tqc_plan_cost_report.argtypes = [vp, vp]
+        L.tqc_plan_cost_report.restype = ctypes.c_int
         for name in ["tqc_hss_norms", "tqc_hss_select", "tqc_network_select"]:
             getattr(L, name).restype = ctypes.c_int
         for name in ["tqc_batch_status", "tqc_batch_inject_stall", "tqc_costmodel_create", "tqc_costmodel_destroy",
@@ -224,6 +231,46 @@ class Network:
             self.close()
         except Exception:
             pass
+
+
+class CutOpts(ctypes.Structure):
+    _fields_ = [("w_max", ctypes.c_int32), ("s_max", ctypes.c_int32), ("k_t", ctypes.c_int32),
+                ("k_sweep_max", ctypes.c_int32), ("q_max", ctypes.c_double), ("t_gate", ctypes.c_double),
+                ("t_meas", ctypes.c_double), ("shots_log2_min", ctypes.c_int32), ("shots_log2_max", ctypes.c_int32),
+                ("n_qpus", ctypes.c_int32), ("cost_free_qubits", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("costmodel_path", ctypes.c_char_p)]
+
+
+class CutResult(ctypes.Structure):
+    _fields_ = [("n_sub", ctypes.c_int32), ("n_cuts", ctypes.c_int32), ("k_t", ctypes.c_int32),
+                ("max_width", ctypes.c_int32), ("t_qpu", ctypes.c_double), ("t_classical", ctypes.c_double),
+                ("t_total", ctypes.c_double), ("cutqc_mults", ctypes.c_double), ("tensorqc_mults", ctypes.c_double)]
+
+
+class CostReport(ctypes.Structure):
+    _fields_ = [("cutqc_mults_per_state", ctypes.c_double), ("tensorqc_mults_per_state", ctypes.c_double),
+                ("ratio", ctypes.c_double), ("plan_mults", ctypes.c_double), ("plan_mults_per_state", ctypes.c_double),
+                ("k_max", ctypes.c_int32), ("tn_upper_bound", ctypes.c_double)]
+
+
+def find_cuts(n_qubits, gates, **opts):
+    """Cut finder (tqc_find_cuts): ``gates`` is a list of qubit tuples (one or
+    two qubits) in time order; keyword options are tqc_cut_opts fields.
+    Returns (per-gate subcircuit ids, result dict)."""
+    o = CutOpts()
+    lib().tqc_cut_opts_default(ctypes.byref(o))
+    for k, v in opts.items():
+        if k == "costmodel_path":
+            v = v.encode() if v else None
+        setattr(o, k, v)
+    gq = np.full((max(len(gates), 1), 2), -1, dtype=np.int32)
+    for g, qs in enumerate(gates):
+        gq[g, :len(qs)] = qs
+    part = np.zeros(max(len(gates), 1), dtype=np.int32)
+    r = CutResult()
+    _check(lib().tqc_find_cuts(n_qubits, len(gates), gq.ctypes.data, ctypes.byref(o), part.ctypes.data,
+                               ctypes.byref(r)))
+    return part[:len(gates)].tolist(), {f: getattr(r, f) for f, _ in CutResult._fields_}
 
 
 class Plan:
@@ -356,6 +403,13 @@ class Plan:
         _check(lib().tqc_contract_noalloc(self.handle, ctypes.cast(ptrs, ctypes.c_void_p), in_dtype,
                                           None if fb is None else fb.ctypes.data, out.data_ptr(), dt,
                                           _stream_ptr(stream)))
+
+    def cost_report(self):
+        """Multiplications of this plan against the brute-force
+        reconstruction (tqc_plan_cost_report)."""
+        r = CostReport()
+        _check(lib().tqc_plan_cost_report(self.handle, ctypes.byref(r)))
+        return {f: getattr(r, f) for f, _ in CostReport._fields_}
 
     def features(self):
         """The plan's TQC_PLAN_FEATURES cost-model features (float32)."""
