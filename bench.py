@@ -77,6 +77,9 @@ def parse():
     ap.add_argument("--pe-train", type=int, default=40)
     ap.add_argument("--pe-test", type=int, default=12)
     ap.add_argument("--pe-candidates", type=int, default=6)
+    ap.add_argument("--states", type=int, default=0,
+                    help="instead: time tqc_contract_states on this many grid30 states")
+    ap.add_argument("--cuts", action="store_true", help="instead: the cut finder on the 48-qubit QAOA circuit")
     ap.add_argument("--no-sub", action="store_true",
                     help="skip the tensor_bound and batched sub-records of the default line")
     ap.add_argument("--sub-steps", type=int, default=5, help="timed steps of each sub-record")
@@ -141,6 +144,11 @@ class ClockSampler:
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(rows[0][2]), "samples": len(rows),
                 "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit()),
                 "reasons": reasons}
+
+
+def step_dtypes(desc):
+    """The operand types the plan's steps compute in, e.g. "bf16x3+tf32"."""
+    return "+".join(sorted({s_["prec"] for s_ in desc["steps"]})) or "f64"
 
 
 def step_bytes(st, out_bytes):
@@ -369,6 +377,138 @@ def run_batch(args):
     return 0
 
 
+def fp32_alu_peak():
+    """FP32 CUDA-core peak of the part in TFLOP/s: 152 SMs x 128 FP32 lanes x
+    2 flop per FMA x the maximum SM clock (2070 MHz) = 80.5."""
+    return 152 * 128 * 2 * 2.070e9 / 1e12
+
+
+def measure_states(args, count=1_000_000, steps=None, warmup=None):
+    """Arbitrary state lists (§VII-C reconstructs one million arbitrary
+    states): ``count`` uniformly drawn states of the grid30 network through
+    tqc_contract_states (the fused single-state kernel), device-timed, the
+    list's host-to-device copy included in each call."""
+    import torch
+    import oracle
+    from gen import workloads
+    from paper_2502_03445_gb300 import tqc
+    steps = steps or args.steps
+    warmup = max(3, warmup or args.warmup)
+    net = workloads.grid30(0)
+    h = tqc.Network(net)
+    p = tqc.Plan(h, free_qubits=[])
+    d = p.describe()
+    st = np.random.Generator(np.random.PCG64(17)).integers(0, 1 << net.n_qubits, size=count, dtype=np.uint64)
+    out = torch.empty(count, dtype=torch.float32, device="cuda")
+    for _ in range(warmup):
+        p.contract_states(st, out)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(torch.cuda.current_device()) if not args.no_clocks else None
+    t_end = time.time() + (0.0 if args.no_clocks else 0.6)
+    while time.time() < t_end:
+        p.contract_states(st, out)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        p.contract_states(st, out)
+    e1.record()
+    torch.cuda.synchronize()
+    clocks = sampler.stop() if sampler else None
+    ms = e0.elapsed_time(e1) / steps
+    macs = sum(2 ** (s_["log2_m"] + s_["log2_n"] + s_["log2_k"]) for s_ in d["steps"])
+    achieved = 2.0 * macs * count / (ms / 1e3) / 1e12
+    pk = fp32_alu_peak()
+    k = 2048
+    z = oracle.total_mass(net)
+    want = oracle.recon_states(net, st[:k]) / z
+    err = np.abs(out[:k].double().cpu().numpy() - want)
+    p.close()
+    h.close()
+    del out
+    torch.cuda.empty_cache()
+    return {"workload": f"grid30: {count} uniformly drawn states of 2^30, one tqc_contract_states call per step "
+                        f"(the list's 8-byte states copied host to device inside the call)",
+            "value": count / (ms / 1e3), "unit": "states/s", "ms_per_step": ms, "steps": steps, "warmup": warmup,
+            "form": d["states_form"], "macs_per_state": macs,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": pk, "unit": "TFLOP/s", "frac": achieved / pk,
+                         "traffic": None, "kernel": "states_kernel",
+                         "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
+                         "algorithmic_flops_per_launch": 2.0 * macs * count},
+            "clocks": clocks, "gpu_launches": steps,
+            "error_vs_oracle": {"states": k, "oracle": "A", "max_abs": float(err.max()),
+                                "max_abs_rel_to_max_p": float(err.max() / np.abs(want).max())}}
+
+
+def measure_bin_stream(args, n_bins=16):
+    """Reuse of intermediates across bins: grid30 bins of 2^26 states whose
+    four fixed qubits all belong to the subcircuit that enters the last
+    step, so consecutive bins differ only in that subcircuit's fixed bits;
+    ms per bin with the plan's reuse and with TQC_FLAG_NO_REUSE."""
+    import torch
+    from gen import workloads
+    from paper_2502_03445_gb300 import tqc
+    net = workloads.grid30(0)
+    h = tqc.Network(net)
+    probe = tqc.Plan(h)
+    last = probe.describe()["steps"][-1]
+    m = len(net.nodes)
+    leaf = last["b"] if last["b"] < m else last["a"]
+    probe.close()
+    if leaf >= m:
+        h.close()
+        return {"skipped": "the last step joins two intermediates"}
+    fixed_q = net.nodes[leaf].out_qubits[:4]
+    free = [q for q in range(net.n_qubits) if q not in fixed_q]
+    res = {}
+    for name, flags in (("reuse", 0), ("no_reuse", tqc.FLAG_NO_REUSE)):
+        p = tqc.Plan(h, free_qubits=free, flags=flags)
+        out = torch.empty(p.out_elems, dtype=torch.float32, device="cuda")
+        fbs = []
+        for b in range(n_bins):
+            fb = np.zeros(net.n_qubits, np.uint8)
+            fb[fixed_q] = [(b >> i) & 1 for i in range(4)]
+            fbs.append(fb)
+        for fb in fbs[:3]:
+            p.contract(out, fixed_bits=fb)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for fb in fbs:
+            p.contract(out, fixed_bits=fb)
+        e1.record()
+        torch.cuda.synchronize()
+        d = p.describe()
+        res[name] = {"ms_per_bin": e0.elapsed_time(e1) / n_bins, "reused_leaves": d["reused_leaves"],
+                     "reused_steps": d["reused_steps"]}
+        p.close()
+        del out
+    h.close()
+    torch.cuda.empty_cache()
+    res["workload"] = (f"grid30: {n_bins} bins of 2^26 states; fixed qubits {fixed_q} all in subcircuit {leaf}, "
+                       f"which enters the last step")
+    res["speedup_of_reuse"] = res["no_reuse"]["ms_per_bin"] / res["reuse"]["ms_per_bin"]
+    return res
+
+
+def measure_cut_finder():
+    """The cut finder (§VI, Alg. 2/3) on the 48-qubit QAOA p=1 circuit:
+    subcircuits of at most 16 qubits and half the circuit's two-qubit gates,
+    K_t swept 1..16, T_QPU by Eq. qpu_runtime (10 QPUs), T_classical the
+    planner's estimate for a 2^20-state bin."""
+    from gen import circuits
+    from paper_2502_03445_gb300 import tqc
+    n, gates = circuits.qaoa_regular(48, 4000)
+    gq = [tuple(qs) for _, qs, _ in gates]
+    n2q = sum(1 for q in gq if len(q) == 2)
+    t0 = time.perf_counter()
+    part, r = tqc.find_cuts(n, gq, w_max=16, s_max=max(1, n2q // 2), k_t=0, k_sweep_max=16, cost_free_qubits=20)
+    r["find_s"] = time.perf_counter() - t0
+    r["circuit"] = f"QAOA p=1, random 3-regular graph, n = {n}, {n2q} two-qubit gates"
+    r["cost_ratio_cutqc_over_tensorqc"] = r["cutqc_mults"] / r["tensorqc_mults"] if r["tensorqc_mults"] else None
+    return r
+
+
 def tensor_peak(prec, bf16):
     """(peak in algorithmic TFLOP/s, how it is derived) of a tensor-core step."""
     if prec == "bf16x3":
@@ -469,7 +609,7 @@ def measure_tensor_bound(args, workload="qaoa48", steps=None, warmup=None):
     return {"workload": f"{workload}: bin of 2^24 states, {net.n_cuts} cuts, {len(net.nodes)} subcircuits, "
                         f"node tensors drawn bin-restricted",
             "value": (1 << net.n_qubits) / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "steps": steps,
-            "warmup": warmup, "dtype": desc["precision"],
+            "warmup": warmup, "dtype": step_dtypes(desc),
             "slices": info["n_slices"], "sliced": desc["sliced"],
             "plan": [[s_["log2_m"], s_["log2_n"], s_["log2_k"], s_["class"], s_["prec"], s_["tile"],
                       s_["ksplit"], s_["kblk"]] for s_ in desc["steps"]],
@@ -659,6 +799,14 @@ def main():
         return run_planner_eval(args)
     if args.hss:
         return run_hss(args)
+    if args.states:
+        import torch
+        torch.cuda.set_device(0)
+        print(json.dumps(measure_states(args, args.states)), flush=True)
+        return 0
+    if args.cuts:
+        print(json.dumps(measure_cut_finder()), flush=True)
+        return 0
     if args.workload != "grid30":
         return run_workload(args)
     ws, rank, local = dist_env()
@@ -684,6 +832,7 @@ def main():
     setup = {"upload_ms": 1e3 * (t1 - t0), "upload_bytes": int(sum(nd.data.nbytes for nd in net.nodes)),
              "planning_ms": 1e3 * (t2 - t1)}
     desc = plan.describe()
+    cost = plan.cost_report()
     out = torch.empty(plan.out_elems, dtype=torch.float32, device="cuda")
     probs_per_step = plan.out_elems
 
@@ -748,7 +897,7 @@ def main():
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": desc["precision"], "data": "synthetic",
+            "vs_baseline": None, "dtype": step_dtypes(desc), "data": "synthetic",
             "config": {"workload": WORKLOAD if free is None else
                        WORKLOAD.replace("full 2^30 output", f"bin of the lowest {args.free_qubits} qubits"),
                        "plan": [[s_["log2_m"], s_["log2_n"], s_["log2_k"], s_["class"], s_["tile"],
@@ -758,7 +907,7 @@ def main():
                        "l2": "working set 4.6 GB > 129 MB L2, no flush needed",
                        "parallelism": f"weak x{ws}, one network per GPU"},
             "roofline": roof, "gpu_launches": desc["launches_per_contract"] * args.steps,
-            "clocks": clocks, "setup": setup}
+            "clocks": clocks, "setup": setup, "cost_report": cost}
 
     # plain FP32 CUDA-core form on the same network
     if not args.no_plain:
@@ -804,12 +953,16 @@ def main():
     h.close()
     del out
     torch.cuda.empty_cache()
-    # sub-records at one GPU: the tensor-bound bin and the batched launch
+    # sub-records at one GPU: the tensor-bound bin, the batched launch, state
+    # lists, reuse across bins, the cut finder
     if ws == 1 and not args.no_sub:
         tb = measure_tensor_bound(args, "qaoa48", steps=args.sub_steps, warmup=args.warmup)
         tb.pop("_spec")
         line["tensor_bound"] = tb
         line["batched"] = measure_batched(args, 256, steps=args.sub_steps, warmup=args.warmup)
+        line["states"] = measure_states(args, 1_000_000, steps=args.sub_steps, warmup=args.warmup)
+        line["bin_stream"] = measure_bin_stream(args)
+        line["cut_finder"] = measure_cut_finder()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:
