@@ -53,6 +53,7 @@ struct SStep {
     int32_t a_off, b_off;   // shared-memory offsets of the operands
     int32_t tm, tn;         // register tile of a thread (rows strided by M / tm, columns by N / tn)
     int32_t ksplit;         // K ranges of one output tile (summed through the reduction buffer)
+    int32_t tab_off;        // shared-memory offset of the result offsets of rows (M) then columns (N)
 };
 
 struct SProgram {
@@ -68,13 +69,28 @@ struct SProgram {
 // float4 access and spreads rows over the banks.
 __host__ __device__ __forceinline__ int pitch_of(int k) { return k >= 4 ? k + 4 : k; }
 
-__global__ void __launch_bounds__(ST_THREADS)
+__global__ void __launch_bounds__(ST_THREADS, 3)
     states_kernel(const __grid_constant__ SProgram P, const uint64_t *__restrict__ states, int64_t n, void *out,
                   int out_f64, const double *zinfo) {
     extern __shared__ __align__(16) float sm[];
     __shared__ int64_t proj[ST_MAX_LEAVES];
     const int tid = threadIdx.x;
     const double scale = zinfo[1];
+    // Every state runs the same program: the place of result row r and column
+    // c in the consumer's padded operand is tab[r] + tab[M + c] (the row and
+    // column bits are disjoint, so the deposit of (r, c) splits into two
+    // parts), computed once per CTA.
+    for (int si = 0; si < P.n_steps; ++si) {
+        const SStep &S = P.step[si];
+        const int M = 1 << S.mb, N = 1 << S.nb;
+        int *tab = (int *)(sm + S.tab_off);
+        const int ck = S.c_kb < 0 ? 1 : 1 << S.c_kb, pc = pitch_of(ck);
+        for (int i = tid; i < M + N; i += ST_THREADS) {
+            const uint32_t d = i < M ? pdep32((uint32_t)i, S.maskR) : pdep32((uint32_t)(i - M), S.maskC);
+            tab[i] = S.c_kb < 0 ? 0 : (int)(d >> S.c_kb) * pc + (int)(d & (uint32_t)(ck - 1));
+        }
+    }
+    __syncthreads();
     for (int64_t s = blockIdx.x; s < n; s += gridDim.x) {
         const uint64_t x = states[s];
         if (tid < P.n_leaves) {
@@ -106,9 +122,9 @@ __global__ void __launch_bounds__(ST_THREADS)
                 const float *row = P.leaf[src].table + (proj[src] << P.leaf[src].row_log2);
                 float *dst = sm + (op ? S.b_off : S.a_off);
                 if (K >= 4) {
-                    const int q = K >> 2;
-                    for (int i = tid; i < rows * q; i += ST_THREADS) {
-                        const int r = i / q, k4 = i - r * q;
+                    const int lq = S.kb - 2;  // float4s per row: K / 4
+                    for (int i = tid; i < rows << lq; i += ST_THREADS) {
+                        const int r = i >> lq, k4 = i & ((1 << lq) - 1);
                         *(float4 *)(dst + r * pk + 4 * k4) = __ldg((const float4 *)row + i);
                     }
                 } else {
@@ -119,9 +135,12 @@ __global__ void __launch_bounds__(ST_THREADS)
             const float *A = sm + S.a_off, *B = sm + S.b_off;
             const int tm = S.tm, tn = S.tn;
             const int rstride = M / tm, cstride = N / tn;
+            const int lc = __ffs(cstride) - 1, lt = lc + __ffs(rstride) - 1;  // log2 of cstride, n_tiles
             const int n_tiles = rstride * cstride;
             const int kc = K / S.ksplit;
             float *red = sm + P.red_off;
+            const int *tab = (const int *)(sm + S.tab_off);
+            float *res = sm + S.c_off;
             // result element (r, c) -> its place in the consumer's padded operand
             auto put = [&](int r, int c, float v) {
                 if (S.c_kb < 0) {
@@ -130,12 +149,11 @@ __global__ void __launch_bounds__(ST_THREADS)
                     else ((float *)out)[s] = (float)d;
                     return;
                 }
-                const uint32_t i = pdep32((uint32_t)r, S.maskR) | pdep32((uint32_t)c, S.maskC);
-                sm[S.c_off + (int)(i >> S.c_kb) * pitch_of(1 << S.c_kb) + (int)(i & ((1u << S.c_kb) - 1))] = v;
+                res[tab[r] + tab[M + c]] = v;
             };
             for (int u = tid; u < n_tiles * S.ksplit; u += ST_THREADS) {
-                const int t = u % n_tiles, ks = u / n_tiles;
-                const int rt = t / cstride, ct = t - rt * cstride;
+                const int t = u & (n_tiles - 1), ks = u >> lt;
+                const int rt = t >> lc, ct = t & (cstride - 1);
                 float acc[4][4];
 #pragma unroll
                 for (int i = 0; i < 4; ++i)
@@ -269,6 +287,8 @@ bool build_program(const Plan &p, SProgram *P, std::string *why) {
         SStep &S = P->step[s];
         S.a_off = S.a_src >= 0 ? 0 : P->step[-1 - S.a_src].c_off;
         S.b_off = S.b_src >= 0 ? (int32_t)align4(stg[0]) : P->step[-1 - S.b_src].c_off;
+        S.tab_off = (int32_t)off;  // offset tables of the epilogue (ints)
+        off += align4(((int64_t)1 << S.mb) + ((int64_t)1 << S.nb));
     }
     if (off > ST_MAX_SMEM_FLOATS) return *why = "intermediates exceed shared memory", false;
     P->smem_floats = (int32_t)std::max<int64_t>(off, 4);
