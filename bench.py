@@ -491,6 +491,65 @@ def measure_bin_stream(args, n_bins=16):
     return res
 
 
+def measure_learned_planner(args, n_train=16, n_small=12, n_test=8):
+    """The learned planner against the planners without it: the MLP cost
+    model (3 x 128, the library's own GPU kernels) is trained on the
+    planner's timings of the candidate plans of 28-30-qubit networks (4-6
+    subcircuits) and smaller ones; on held-out 28-30-qubit networks the plans
+    chosen by the learned planner, the analytic ranking of the same
+    candidates, TQC_PLANNER_AUTO and the greedy planner are timed against the
+    fastest candidate (geometric means)."""
+    import math
+    import torch
+    from gen import workloads
+    from paper_2502_03445_gb300 import costmodel, tqc
+    t0 = time.perf_counter()
+    train, test = [], []
+    for kind, seed in [("g30", 9800 + i) for i in range(n_train + n_test)] + \
+                      [("small", 9000 + i) for i in range(n_small)]:
+        net = workloads.planner_network(seed, kind)
+        h = tqc.Network(net, dtype=tqc.F32)
+        recs = costmodel.collect(h, precision=args.precision, max_candidates=8, reps=5)
+        (test.append((net, recs)) if kind == "g30" and seed >= 9800 + n_train else train.extend(recs))
+        h.close()
+    X, y = costmodel.dataset(train)
+    cm = tqc.CostModel(X.shape[1], seed=0)
+    t1 = time.perf_counter()
+    cm.train(X, y, epochs=400, batch=32, lr=1e-3, seed=1)
+    t_train = time.perf_counter() - t1
+    path = os.path.join(tempfile.mkdtemp(), "costmodel.bin")
+    cm.save(path)
+    ratios = {"learned": [], "analytic_ranking": [], "auto": [], "greedy": []}
+    err = {"mlp": [], "analytic": []}
+    for net, recs in test:
+        meas = np.array([r["seconds"] for r in recs])
+        best = meas.min()
+        ana = np.log([r["predicted_s"] for r in recs])
+        pred = costmodel.predicted_log_seconds(cm, recs)
+        err["mlp"].append(float(np.mean(np.abs(pred - np.log(meas)))))
+        err["analytic"].append(float(np.mean(np.abs(ana - np.log(meas)))))
+        ratios["analytic_ranking"].append(meas[int(np.argmin(ana))] / best)
+        h = tqc.Network(net, dtype=tqc.F32)
+        out = torch.empty(1 << net.n_qubits, dtype=torch.float32, device="cuda")
+        for name, pl in (("learned", tqc.PLANNER_LEARNED), ("auto", tqc.PLANNER_AUTO), ("greedy", tqc.PLANNER_GREEDY)):
+            p = tqc.Plan(h, precision=args.precision, planner=pl,
+                         costmodel_path=path if pl == tqc.PLANNER_LEARNED else None)
+            ratios[name].append(costmodel.time_plan(p, out, reps=5) / best)
+            p.close()
+        del out
+        h.close()
+    cm.close()
+    torch.cuda.empty_cache()
+    gm = {k: float(math.exp(np.mean(np.log(v)))) for k, v in ratios.items()}
+    return {"workload": f"held-out networks: {n_test} of 27-30 qubits, 4-6 subcircuits (Gaussian values, timing "
+                        f"only); trained on {n_train} such and {n_small} of 20-24 qubits",
+            "plan_time_over_best_candidate": gm, "learned_speedup_over_auto": gm["auto"] / gm["learned"],
+            "learned_speedup_over_analytic_ranking": gm["analytic_ranking"] / gm["learned"],
+            "held_out_mean_abs_log_error": {k: float(np.mean(v)) for k, v in err.items()},
+            "train_records": len(train), "collect_and_eval_s": time.perf_counter() - t0, "train_s": t_train,
+            "model": "MLP 32-128-128-128-1 (ReLU), MSE on log(measured / analytic seconds), own GPU kernels"}
+
+
 def measure_cut_finder():
     """The cut finder (§VI, Alg. 2/3) on the 48-qubit QAOA p=1 circuit:
     subcircuits of at most 16 qubits and half the circuit's two-qubit gates,
@@ -963,6 +1022,7 @@ def main():
         line["states"] = measure_states(args, 1_000_000, steps=args.sub_steps, warmup=args.warmup)
         line["bin_stream"] = measure_bin_stream(args)
         line["cut_finder"] = measure_cut_finder()
+        line["learned_planner"] = measure_learned_planner(args)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:

@@ -148,6 +148,22 @@ def batch_recipe(count: int = 256, n_lo: int = 16, n_hi: int = 28, seed0: int = 
     return nets, redraws
 
 
+def planner_network(seed: int, kind: str = "g30"):
+    """Timing-only networks for the learned planner (Gaussian FP32 values):
+    ``g30`` -- 27-30 qubits, 4-6 subcircuits, m+5..m+7 cuts, widths <= 11
+    (the 30-qubit grid workload's neighbourhood: sub-millisecond plans whose
+    kernel classes the analytic model ranks least well); ``small`` -- 20-24
+    qubits, 5-7 subcircuits, m+2..m+6 cuts, widths <= 12."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    if kind == "g30":
+        n, m = int(rng.integers(27, 31)), int(rng.integers(4, 7))
+        cuts = int(rng.integers(m + 5, m + 8))
+        return tensors.random_shape_network(n, m, cuts, 11, seed=seed, max_node_cuts=7)
+    n, m = int(rng.integers(20, 25)), int(rng.integers(5, 8))
+    cuts = int(rng.integers(m + 2, m + 7))
+    return tensors.random_shape_network(n, m, cuts, 12, seed=seed, max_node_cuts=7)
+
+
 HSS_FAMILIES = ("ghz", "w", "regular", "supremacy")
 
 

@@ -88,7 +88,8 @@ enum {
 /* plan flags */
 enum {
     TQC_FLAG_NO_RENORM = 1,      /* skip division by the total mass Z (Z still reported) */
-    TQC_FLAG_NO_REUSE = 2        /* recompute every intermediate on every tqc_contract (see there) */
+    TQC_FLAG_NO_REUSE = 2,       /* recompute every intermediate on every tqc_contract (see there) */
+    TQC_FLAG_NO_FUSE = 4         /* run every step as its own kernel (no fused step pairs) */
 };
 
 /*
@@ -165,7 +166,13 @@ TQC_API void tqc_plan_opts_default(tqc_plan_opts *opts);
  * Plan the contraction (host only; no device work): contraction order
  * (§III-E-1), slicing of the most size-reducing cut edges until inputs, then
  * intermediates, fit the budget (§III-E-2), per-step kernel class, operand
- * precision and tensor layouts.
+ * precision and tensor layouts.  Two consecutive split-BF16 tensor-core
+ * steps whose layouts line up (the first with K = 64 writing the row operand
+ * of the second, K = 256 and N = 128; each 128 x 256 tile of the first
+ * result is one 128-row tile of the second step's operand) are marked to run
+ * as one kernel that keeps the intermediate on chip ("fuse" in
+ * tqc_plan_describe: 1 on the first step, 2 on the second), unless
+ * TQC_FLAG_NO_FUSE is set.
  */
 TQC_API tqc_status tqc_plan(tqc_net_t net, const tqc_plan_opts *opts, tqc_plan_t *out);
 

@@ -304,6 +304,7 @@ tqc_status exec_autotune(Plan *p, void *d_out, int out_dtype, cudaStream_t s) {
     int *d_err = (int *)(p->d_zinfo + 2);
     tqc_status result = TQC_OK;
     for (StepPlan &sp : p->steps) {
+        if (sp.fuse) continue;  // a fused pair has one configuration
         const TensorPlan &tc = p->tensors[sp.c];
         int mode = sp.final ? (sliced ? EPI_F64_SET : (out_dtype == TQC_F64 ? EPI_OUT_F64 : EPI_OUT_F32))
                             : epi_mode_of(tc.storage);
@@ -528,7 +529,33 @@ tqc_status exec_run(Plan &pl, const ExecCtx &c, const uint8_t *fixed_bits, void 
         }
         for (size_t si = 0; si < p->steps.size(); ++si) {
             const StepPlan sp = step_of(p->steps[si]);
+            if (sp.fuse == 2) continue;  // ran inside the previous step's fused kernel
             if (sl > 0 && !p->tensors[sp.c].slice_dep) continue;
+            if (sp.fuse == 1) {
+                // steps si and si + 1 as one kernel: the intermediate stays on chip
+                const StepPlan sp1 = step_of(p->steps[si + 1]);
+                if (keep && (*keep)[(size_t)sp1.c]) continue;
+                StepArgs a0 = step_args(*p, p->tensors, sp, c.ws, TileShape{7, 6});
+                StepArgs a1 = step_args(*p, p->tensors, sp1, c.ws, TileShape{7, 6});
+                const TensorPlan &t1 = p->tensors[sp1.c];
+                a1.epi.zinfo = c.zinfo;
+                a1.epi.out = ws_ptr(c.ws, t1.offset);
+                if (t1.storage == ST_BF16X2) a1.epi.out_lo = ws_ptr(c.ws, t1.offset + t1.plane_bytes);
+                a1.epi.mode = epi_mode_of(t1.storage);
+                cudaEvent_t ev[2] = {nullptr, nullptr};
+                if (c.profile) {
+                    TQC_CUDA(cudaEventCreate(&ev[0]), "event");
+                    TQC_CUDA(cudaEventCreate(&ev[1]), "event");
+                    TQC_CUDA(cudaEventRecord(ev[0], s), "event record");
+                }
+                TQC_CUDA(launch_fused_pair(a0, a1, sp.maskR, sp.maskC, d_err, s), "fused step launch");
+                if (c.profile) {
+                    TQC_CUDA(cudaEventRecord(ev[1], s), "event record");
+                    if (p->step_events.size() < p->steps.size()) p->step_events.resize(p->steps.size());
+                    p->step_events[si].push_back({(void *)ev[0], (void *)ev[1]});
+                }
+                continue;
+            }
             if (keep && (*keep)[(size_t)sp.c]) continue;
             StepArgs a = step_args(*p, p->tensors, sp, c.ws, tile_of(sp));
             const TensorPlan &tc = p->tensors[sp.c];

@@ -37,6 +37,14 @@ TileShape umma_tile(int cfg);
 cudaError_t launch_umma_step(int cfg, int prec, const StepArgs &a, int *d_err, cudaStream_t s);
 cudaError_t umma_make_maps(int prec, const StepArgs &a, int bn, void *maps_out);  // 4 CUtensorMap
 
+// Fused pair of tensor-core steps (fused.cu): whether steps s and s + 1 of a
+// plan qualify, the launch (a0: step s's operands; a1: step s + 1's operands
+// and epilogue), and the test hook shared with tqc_step_inject_stall.
+bool fused_pair_ok(const Plan &p, size_t s);
+cudaError_t launch_fused_pair(const StepArgs &a0, const StepArgs &a1, uint64_t maskR0, uint64_t maskC0, int *d_err,
+                              cudaStream_t s);
+void fused_set_stall(int enable);
+
 // Argument blocks the executor builds (executor.cu), reused by the batched launch.
 IngestArgs exec_leaf_args(const Plan &p, const TensorPlan &t, int j, const uint8_t *fixed);
 StepArgs exec_step_args(const Plan &p, const StepPlan &st, TileShape tile);

@@ -19,6 +19,7 @@
 #include <limits>
 #include <sstream>
 
+#include "launch.h"
 #include "tqc_internal.h"
 
 namespace tqc {
@@ -796,6 +797,13 @@ tqc_status build_plan(Net *net, const tqc_plan_opts &o, Plan *p) {
     p->ws_bytes = assign_offsets(B, false, &p->acc_offset, need_acc, p->out_elems());
     p->tensors = std::move(B.t);
     p->steps = std::move(B.s);
+    // consecutive tensor-core steps whose layouts let the intermediate stay on chip
+    if (!(p->flags & TQC_FLAG_NO_FUSE))
+        for (size_t s = 0; s + 1 < p->steps.size(); ++s)
+            if (!p->steps[s].fuse && fused_pair_ok(*p, s)) {
+                p->steps[s].fuse = 1;
+                p->steps[s + 1].fuse = 2;
+            }
 
     NetBits zb = nb;  // Z uses the same slices; each slice adds its scalar
     Built Z = build_steps(*p, zb, pairs, prec, true);
@@ -859,7 +867,7 @@ std::string plan_describe(const Plan &pl) {
            << (st.klass == KC_UMMA ? "tcgen05" : "simt") << "\",\"prec\":\""
            << (st.klass == KC_UMMA ? prec_name(st.prec) : "fp32") << "\",\"out_layout\":" << mode_str(p->tensors[st.c].layout)
            << ",\"mask_r\":" << st.maskR << ",\"mask_c\":" << st.maskC << ",\"tile\":" << st.tile
-           << ",\"ksplit\":" << st.ksplit << ",\"kblk\":" << (st.kblk ? 1 : 0) << "}";
+           << ",\"ksplit\":" << st.ksplit << ",\"kblk\":" << (st.kblk ? 1 : 0) << ",\"fuse\":" << st.fuse << "}";
     }
     os << "],\"layouts\":[";
     for (size_t i = 0; i < p->tensors.size(); ++i) os << (i ? "," : "") << mode_str(p->tensors[i].layout);
@@ -870,8 +878,8 @@ std::string plan_describe(const Plan &pl) {
     if (p->m == 1) launches += 1;
     else {
         for (int j = 0; j < p->m; ++j) launches += p->tensors[j].slice_dep ? p->n_slices() : 1;
-        for (auto &st : p->steps)  // a K-split step adds its reduce pass
-            launches += (p->tensors[st.c].slice_dep ? p->n_slices() : 1) * (st.ksplit > 1 ? 2 : 1);
+        for (auto &st : p->steps)  // a K-split step adds its reduce pass; a fused pair is one launch
+            if (st.fuse != 2) launches += (p->tensors[st.c].slice_dep ? p->n_slices() : 1) * (st.ksplit > 1 ? 2 : 1);
         if (p->n_slices() > 1) launches += 1;
     }
     os << "],\"launches_per_contract\":" << launches << ",\"total_mass_launches\":" << z_launches;

@@ -101,6 +101,7 @@ struct StepPlan {
     int tile = 0;                 // tile configuration (autotuner)
     int ksplit = 1;               // K ranges run by separate CTAs (final tensor-core steps with few tiles)
     bool kblk = false;            // operands stored K-blocked: [K / 64][rows][64] (tensor-core steps with long rows)
+    int fuse = 0;                 // 1: runs with the next step as one fused kernel; 2: run by the previous step's
 };
 
 // ---------------------------------------------------------------- cost model
