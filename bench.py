@@ -444,7 +444,7 @@ def measure_bin_stream(args, n_bins=16):
     """Reuse of intermediates across bins: grid30 bins of 2^26 states whose
     four fixed qubits all belong to the subcircuit that enters the last
     step, so consecutive bins differ only in that subcircuit's fixed bits;
-    ms per bin with the plan's reuse and with TQC_FLAG_NO_REUSE."""
+    ms per bin with TQC_FLAG_REUSE and without it."""
     import torch
     from gen import workloads
     from paper_2502_03445_gb300 import tqc
@@ -461,7 +461,7 @@ def measure_bin_stream(args, n_bins=16):
     fixed_q = net.nodes[leaf].out_qubits[:4]
     free = [q for q in range(net.n_qubits) if q not in fixed_q]
     res = {}
-    for name, flags in (("reuse", 0), ("no_reuse", tqc.FLAG_NO_REUSE)):
+    for name, flags in (("reuse", tqc.FLAG_REUSE), ("no_reuse", 0)):
         p = tqc.Plan(h, free_qubits=free, flags=flags)
         out = torch.empty(p.out_elems, dtype=torch.float32, device="cuda")
         fbs = []

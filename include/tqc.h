@@ -88,7 +88,7 @@ enum {
 /* plan flags */
 enum {
     TQC_FLAG_NO_RENORM = 1,      /* skip division by the total mass Z (Z still reported) */
-    TQC_FLAG_NO_REUSE = 2,       /* recompute every intermediate on every tqc_contract (see there) */
+    TQC_FLAG_REUSE = 2,          /* keep intermediates across tqc_contract calls (see there) */
     TQC_FLAG_NO_FUSE = 4         /* run every step as its own kernel (no fused step pairs) */
 };
 
@@ -216,14 +216,15 @@ TQC_API int32_t tqc_plan_describe(tqc_plan_t plan, char *buf, int32_t size);
  * Steps: bin restriction and layout (ingest), the pairwise contractions,
  * FP64 sum over slices, renormalisation by Z.  The first call allocates the
  * plan's workspace.
- * Reuse across bins: the plan's workspace keeps every leaf operand and
- * intermediate of the previous call.  A call whose bin differs only in the
- * fixed bits of some subcircuits (same tensors, same free set) re-ingests
- * only those subcircuits' leaves and recomputes only the steps that depend
- * on them (not for slice-dependent tensors, which the slice loop rewrites);
- * the last step always runs.  tqc_plan_describe reports what the last call
- * kept; TQC_FLAG_NO_REUSE turns it off, and so does passing the plan to
- * tqc_contract_batch (its launches rewrite the workspace).
+ * Reuse across bins (plans made with TQC_FLAG_REUSE): the plan's workspace
+ * keeps every leaf operand and intermediate of the previous call.  A call
+ * whose bin differs only in the fixed bits of some subcircuits (same
+ * tensors, same free set) re-ingests only those subcircuits' leaves and
+ * recomputes only the steps that depend on them (not slice-dependent
+ * tensors, which the slice loop rewrites); the last step always runs.
+ * tqc_plan_describe reports what the last call kept.  Passing the plan to
+ * tqc_contract_batch turns it off (its launches rewrite the workspace).
+ * Without the flag every call recomputes every step.
  * Device-side failures: every wait of a tensor-core step is bounded; one that
  * gives up sets the plan's error word and its output is wrong.  The word is
  * read only by a call with a non-NULL z_out: that call returns

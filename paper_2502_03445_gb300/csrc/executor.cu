@@ -634,7 +634,7 @@ tqc_status exec_contract(Plan *p, const uint8_t *fixed_bits, void *d_out, int ou
     for (int j = 0; j < p->m; ++j) keys[(size_t)j] = leaf_args(*p, p->tensors[(size_t)j], j, fixed, 0, false).src_base;
     std::vector<char> keep(p->tensors.size(), 0);
     p->reused_leaves = p->reused_steps = 0;
-    if (!(p->flags & TQC_FLAG_NO_REUSE) && !p->batched && p->reuse_ok && p->reuse_version == p->net->version &&
+    if ((p->flags & TQC_FLAG_REUSE) && !p->batched && p->reuse_ok && p->reuse_version == p->net->version &&
         p->m > 1) {
         uint64_t dirty = 0;
         for (int j = 0; j < p->m; ++j)

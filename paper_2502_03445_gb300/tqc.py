@@ -23,7 +23,7 @@ F64, F32 = 0, 1
 PREC_FP32, PREC_TF32, PREC_BF16, PREC_BF16X3, PREC_AUTO = range(5)
 PLANNER_GREEDY, PLANNER_EXHAUSTIVE, PLANNER_LEARNED, PLANNER_AUTO = range(4)
 FLAG_NO_RENORM = 1
-FLAG_NO_REUSE = 2
+FLAG_REUSE = 2
 FLAG_NO_FUSE = 4
 PREC_NAMES = {"fp32": PREC_FP32, "tf32": PREC_TF32, "bf16": PREC_BF16, "bf16x3": PREC_BF16X3, "auto": PREC_AUTO}
 

@@ -1,4 +1,4 @@
-"""Reuse of intermediates across bins (tqc_contract keeps the previous call's
+"""Reuse of intermediates across bins (with TQC_FLAG_REUSE, tqc_contract keeps the previous call's
 leaf operands and intermediates when only some subcircuits' fixed bits
 change).  Every bin of a stream is checked against oracle C (the whole bin
 by FP64 pairwise contraction) at the FP32 gate, with what each call kept
@@ -50,7 +50,7 @@ def test_stream_over_one_subcircuits_fixed_bits(precision):
     h = tqc.Network(net)
     fixed_q = net.nodes[3].out_qubits[:3]
     free = [q for q in range(18) if q not in fixed_q]
-    p = tqc.Plan(h, precision=precision, free_qubits=free, order=ORDER)
+    p = tqc.Plan(h, precision=precision, free_qubits=free, order=ORDER, flags=tqc.FLAG_REUSE)
     out = torch.empty(p.out_elems, dtype=torch.float32, device="cuda")
     n_steps = len(p.describe()["steps"])
     for k, bits in enumerate(itertools.product([0, 1], repeat=3)):
@@ -68,12 +68,12 @@ def test_stream_over_one_subcircuits_fixed_bits(precision):
 
 
 def test_invalidation():
-    """New tensors, a first-contracted subcircuit's bits, the per-state path
-    and TQC_FLAG_NO_REUSE all give correct results."""
+    """New tensors, a first-contracted subcircuit's bits and the per-state
+    path give correct results; without TQC_FLAG_REUSE nothing is kept."""
     net = chain(5200)
     free = list(range(14))
     h = tqc.Network(net)
-    p = tqc.Plan(h, precision="bf16x3", free_qubits=free)
+    p = tqc.Plan(h, precision="bf16x3", free_qubits=free, flags=tqc.FLAG_REUSE)
     out = torch.empty(p.out_elems, dtype=torch.float32, device="cuda")
     fixed = np.zeros(18, np.uint8)
     p.contract(out, fixed_bits=fixed)
@@ -100,7 +100,7 @@ def test_invalidation():
     p.contract(out, fixed_bits=fixed)
     check(out, net2, free, fixed)
     p.close()
-    q = tqc.Plan(h, precision="bf16x3", free_qubits=free, flags=tqc.FLAG_NO_REUSE)
+    q = tqc.Plan(h, precision="bf16x3", free_qubits=free)      # without TQC_FLAG_REUSE
     for _ in range(2):
         q.contract(out, fixed_bits=fixed)
         assert q.describe()["reused_steps"] == 0
@@ -113,7 +113,7 @@ def test_sliced_plan_keeps_only_slice_independent_tensors():
     net = chain(5300)
     free = list(range(15))
     h = tqc.Network(net)
-    p = tqc.Plan(h, precision="bf16x3", free_qubits=free, sliced=[7])
+    p = tqc.Plan(h, precision="bf16x3", free_qubits=free, sliced=[7], flags=tqc.FLAG_REUSE)
     out = torch.empty(p.out_elems, dtype=torch.float32, device="cuda")
     for bits in ([0, 0, 0], [1, 0, 1], [1, 1, 1]):
         fixed = np.zeros(18, np.uint8)
