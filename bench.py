@@ -173,7 +173,7 @@ def traffic_record(kernel):
     path = os.path.join(ROOT, "profiles", f"{kernel}_traffic.md")
     csrc = os.path.join(ROOT, "paper_2502_03445_gb300", "csrc")
     srcs = [os.path.join(csrc, "umma.cu" if kernel.startswith("umma") else "simt.cu"),
-            os.path.join(csrc, "device_common.cuh")]
+            os.path.join(csrc, "device_common.cuh"), os.path.join(csrc, "tc_ptx.cuh")]
     try:
         rec = {}
         with open(path) as f:
@@ -586,12 +586,20 @@ def path_roofline(steps, n_slices, hbm, bf16):
     accumulator once per slice when the plan is sliced."""
     t = 0.0
     for i, st in enumerate(steps):
+        if st.get("fuse") == 2:      # counted with the step before it
+            continue
         last = i == len(steps) - 1
         tb = step_bytes(st, (16 if n_slices > 1 else 4) if last else 4) / (hbm * 1e9)
         tf = 0.0
         if st["class"] == "tcgen05":
             pk, _ = tensor_peak(st["prec"], bf16)
             tf = 2.0 * 2 ** (st["log2_m"] + st["log2_n"] + st["log2_k"]) / (pk * 1e12)
+        if st.get("fuse") == 1:      # a fused pair: the intermediate is neither written nor read
+            nx = steps[i + 1]
+            m, n, k = 2 ** nx["log2_m"], 2 ** nx["log2_n"], 2 ** nx["log2_k"]
+            tb = (step_bytes(st, 0) + 4 * n * k + 4 * m * n) / (hbm * 1e9)
+            pk, _ = tensor_peak(nx["prec"], bf16)
+            tf += 2.0 * m * n * k / (pk * 1e12)
         t += max(tb, tf)
     return t * n_slices * 1e3
 

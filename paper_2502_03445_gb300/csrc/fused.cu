@@ -20,9 +20,10 @@
 //     store    D1 (128 x 128) -> step s + 1's result through the direct
 //              epilogue (its own output mode and layout)
 //
-// Roles (480 threads, one CTA per SM, persistent over units): warp 0 copies
-// A0/B0, warp 1 issues MMAs, warp 2 copies B1 k-blocks, warps 3-6 convert,
-// warps 7-14 store.  Tensor memory: D0 (256 columns) and a double-buffered
+// Roles (608 threads, one CTA per SM, persistent over units): warp 0 copies
+// A0/B0, warp 1 issues MMAs, warp 2 copies B1 k-blocks, warps 3-10 convert
+// (two per tensor-memory lane group, each taking half of the column runs),
+// warps 11-18 store.  Tensor memory: D0 (256 columns) and a double-buffered
 // D1 (2 x 128).  Shared memory: A0/B0 96 KB, B1 and C0' k-block rings of two
 // 32 KB slots each.  Every wait is bounded; a wait that gives up raises the
 // CTA's abort flag and the error word, drains the copies and MMAs in flight,
@@ -44,9 +45,10 @@ namespace {
 
 using namespace tc;
 
-constexpr int F_THREADS = 480;
-constexpr int F_CONVERT0 = 3;   // first convert warp (4 warps)
-constexpr int F_EPI0 = 7;       // first store warp (8 warps)
+constexpr int F_THREADS = 608;
+constexpr int F_CONVERT0 = 3;   // first convert warp
+constexpr int F_CONVERT_WARPS = 8;
+constexpr int F_EPI0 = F_CONVERT0 + F_CONVERT_WARPS;  // first store warp
 constexpr int F_EPI_WARPS = 8;
 constexpr int A0_BYTES = 128 * 128;         // one plane: 128 rows x 64 bf16
 constexpr int B0_BYTES = 256 * 128;
@@ -109,13 +111,13 @@ __global__ void __launch_bounds__(F_THREADS, 1)
         for (int i = 0; i < 2; ++i) {
             mbar_init(&b1_full[i], 1);
             mbar_init(&b1_empty[i], 1);
-            mbar_init(&a1_full[i], 4);
+            mbar_init(&a1_full[i], F_CONVERT_WARPS);
             mbar_init(&a1_empty[i], 1);
             mbar_init(&d1_full[i], 1);
             mbar_init(&d1_empty[i], F_EPI_WARPS);
         }
         mbar_init(d0_full, 1);
-        mbar_init(d0_empty, 4);
+        mbar_init(d0_empty, F_CONVERT_WARPS);
         mbar_init(drain, 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -249,8 +251,9 @@ __global__ void __launch_bounds__(F_THREADS, 1)
         }
     } else if (warp < F_EPI0) {
         // ------------------------------------------------ convert D0 -> C0' k-blocks
-        // lane: D0 row r0 (tensor-memory lane); its C0' bits from A0's row bits
-        const int lane_grp = warp & 3;
+        // lane: D0 row r0 (tensor-memory lane); its C0' bits from A0's row bits;
+        // the warp takes column runs 8 half .. 8 half + 7 of every k-block
+        const int lane_grp = warp & 3, half = (warp - F_CONVERT0) >> 2;
         const int r0 = lane_grp * 32 + lane;
         const uint32_t dR = (uint32_t)pdep64((uint64_t)r0, P.maskR0);
         const uint32_t lane_addr = (uint32_t)(lane_grp * 32) << 16;
@@ -270,9 +273,8 @@ __global__ void __launch_bounds__(F_THREADS, 1)
                     break;
                 }
                 uint8_t *hi = smem + OFF_A1 + sl * 2 * KB_BYTES, *lo = hi + KB_BYTES;
-                // 16 runs of 4 D0 columns (c0 = 16 m + 4 j + i): C0' row r1 = t >> 8, k = t & 63
-#pragma unroll
-                for (int half = 0; half < 2; ++half) {
+                // runs of 4 D0 columns (c0 = 16 m + 4 j + i): C0' row r1 = t >> 8, k = t & 63
+                {
                     uint32_t v[8][4];
 #pragma unroll
                     for (int mm = 0; mm < 8; ++mm)
