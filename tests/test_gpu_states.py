@@ -135,10 +135,10 @@ def test_no_renorm_and_uploads():
 
 def test_qaoa48_per_state_form():
     """The 48-qubit QAOA bin network: single-state intermediates of 4^12
-    floats run per state through the step kernels; 160 uniformly drawn
+    floats run per state through the step kernels; 1024 uniformly drawn
     states against oracle B."""
     net = workloads.qaoa48(0)
-    st = states_of(net.n_qubits, 160, 48)
+    st = states_of(net.n_qubits, 1024, 48)
     h = tqc.Network(net)
     p = tqc.Plan(h, free_qubits=[])
     d = p.describe()
