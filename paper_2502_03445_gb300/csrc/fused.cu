@@ -16,9 +16,7 @@
 //     convert  D0 -> BF16 hi / lo planes of the 4 k-blocks of the C0' tile
 //              (64 K each) in 128-byte-swizzled shared memory, one k-block
 //              at a time, following the bit permutation above
-//     MMA      D1 += C0'_j B1_j^T over the 4 k-blocks j (B1 k-blocks by TMA;
-//              consecutive units alternate the order 0..3 / 3..0 so that the
-//              last two B1 k-blocks of one unit serve the next unit first)
+//     MMA      D1 += C0'_j B1_j^T, j = 0..3 (B1 k-blocks by TMA)
 //     store    D1 (128 x 128) -> step s + 1's result through the direct
 //              epilogue (its own output mode and layout)
 //
@@ -166,34 +164,26 @@ __global__ void __launch_bounds__(F_THREADS, 1)
         }
     } else if (warp == 2) {
         // ------------------------------------------------ B1 k-block copies
-        // k-block k lives in slot k & 1; units alternate the order 0,1,2,3 /
-        // 3,2,1,0, so a unit's first two k-blocks are the two its predecessor
-        // left in the slots and only its last two are copied (all four in the
-        // first unit)
         if (lane == 0) {
-            int64_t lt = 0;
-            int nl[2] = {0, 0};  // copies into each slot
+            int64_t it = 0;
             bool ok = true;
-            for (int64_t u = blockIdx.x; ok && u < P.n_units; u += gridDim.x, ++lt) {
-                for (int p = 0; p < 4; ++p) {
-                    if (lt > 0 && p < 2) continue;
-                    const int k = (lt & 1) ? 3 - p : p, sl = k & 1;
-                    if (!mbar_wait(&b1_empty[sl], (uint32_t)((nl[sl] & 1) ^ 1), abort_flag)) {
+            for (int64_t u = blockIdx.x; ok && u < P.n_units; u += gridDim.x) {
+                for (int j = 0; j < 4; ++j, ++it) {
+                    const int sl = (int)(it & 1);
+                    if (!mbar_wait(&b1_empty[sl], (uint32_t)(((it >> 1) & 1) ^ 1), abort_flag)) {
                         ok = false;
                         break;
                     }
                     uint8_t *dst = smem + OFF_B1 + sl * 2 * KB_BYTES;
                     mbar_expect_tx(&b1_full[sl], 2 * KB_BYTES);
-                    tma_load_2d(dst, &tB1, 64 * k, 0, &b1_full[sl]);
-                    tma_load_2d(dst + KB_BYTES, &tB1l, 64 * k, 0, &b1_full[sl]);
-                    ++nl[sl];
+                    tma_load_2d(dst, &tB1, 64 * j, 0, &b1_full[sl]);
+                    tma_load_2d(dst + KB_BYTES, &tB1l, 64 * j, 0, &b1_full[sl]);
                 }
             }
-            if (!ok) {  // drain the last copy into each slot
-                for (int sl = 0; sl < 2; ++sl) {
-                    if (!nl[sl]) continue;
+            if (!ok) {
+                for (int64_t j = it > 2 ? it - 2 : 0; j < it; ++j) {
                     long long t0 = clock64();
-                    while (!mbar_try_wait(&b1_full[sl], (uint32_t)((nl[sl] - 1) & 1)) && clock64() - t0 < WAIT_CYCLES) {
+                    while (!mbar_try_wait(&b1_full[j & 1], (uint32_t)((j >> 1) & 1)) && clock64() - t0 < WAIT_CYCLES) {
                     }
                 }
             }
@@ -202,7 +192,6 @@ __global__ void __launch_bounds__(F_THREADS, 1)
         // ------------------------------------------------ MMA issuer
         if (lane == 0) {
             int64_t lt = 0, itb = 0;
-            int nf[2] = {0, 0};  // B1 copies waited for, per slot
             bool ok = true;
             const uint32_t d0 = tmem_base;
             for (int64_t u = blockIdx.x; ok && u < P.n_units; u += gridDim.x, ++lt) {
@@ -233,33 +222,25 @@ __global__ void __launch_bounds__(F_THREADS, 1)
                     ok = false;
                     break;
                 }
-                for (int p = 0; p < 4; ++p, ++itb) {
-                    // k-block k of B1 (slot k & 1; a fresh copy except at a unit's
-                    // first two positions, which reuse the previous unit's last
-                    // two) against the p-th converted k-block (A1 slot p & 1)
-                    const int k = (lt & 1) ? 3 - p : p, bs = k & 1, as = (int)(itb & 1);
-                    const bool fresh = lt == 0 || p >= 2;
-                    if (fresh && !mbar_wait(&b1_full[bs], (uint32_t)(nf[bs] & 1), abort_flag)) {
-                        ok = false;
-                        break;
-                    }
-                    if (fresh) ++nf[bs];
-                    if (!mbar_wait(&a1_full[as], (uint32_t)((itb >> 1) & 1), abort_flag)) {
+                for (int j = 0; j < 4; ++j, ++itb) {
+                    const int sl = (int)(itb & 1);
+                    const uint32_t ph = (uint32_t)((itb >> 1) & 1);
+                    if (!mbar_wait(&b1_full[sl], ph, abort_flag) || !mbar_wait(&a1_full[sl], ph, abort_flag)) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t a = smem_u32(smem + OFF_A1 + as * 2 * KB_BYTES), al = a + KB_BYTES;
-                    const uint32_t b = smem_u32(smem + OFF_B1 + bs * 2 * KB_BYTES), bl = b + KB_BYTES;
+                    const uint32_t a = smem_u32(smem + OFF_A1 + sl * 2 * KB_BYTES), al = a + KB_BYTES;
+                    const uint32_t b = smem_u32(smem + OFF_B1 + sl * 2 * KB_BYTES), bl = b + KB_BYTES;
 #pragma unroll
-                    for (int ks = 0; ks < 4; ++ks) {
-                        const uint64_t da = umma_desc(a + 32 * ks, 128), db = umma_desc(b + 32 * ks, 128);
-                        umma<K_BF16X3>(d1, da, db, IDESC1, (p | ks) != 0);
-                        umma<K_BF16X3>(d1, da, umma_desc(bl + 32 * ks, 128), IDESC1, 1u);
-                        umma<K_BF16X3>(d1, umma_desc(al + 32 * ks, 128), db, IDESC1, 1u);
+                    for (int k = 0; k < 4; ++k) {
+                        const uint64_t da = umma_desc(a + 32 * k, 128), db = umma_desc(b + 32 * k, 128);
+                        umma<K_BF16X3>(d1, da, db, IDESC1, (j | k) != 0);
+                        umma<K_BF16X3>(d1, da, umma_desc(bl + 32 * k, 128), IDESC1, 1u);
+                        umma<K_BF16X3>(d1, umma_desc(al + 32 * k, 128), db, IDESC1, 1u);
                     }
-                    if (p < 2) umma_commit(&b1_empty[bs]);  // the slot's content is not needed again
-                    umma_commit(&a1_empty[as]);
+                    umma_commit(&b1_empty[sl]);
+                    umma_commit(&a1_empty[sl]);
                 }
                 if (ok) umma_commit(&d1_full[acc]);
             }
@@ -283,8 +264,7 @@ __global__ void __launch_bounds__(F_THREADS, 1)
             if (*abort_flag) break;
             tc_fence_after();
             bool stop = false;
-            for (int p = 0; p < 4; ++p, ++ita) {
-                const int j = (lt & 1) ? 3 - p : p;  // k-block, in the MMA issuer's order
+            for (int j = 0; j < 4; ++j, ++ita) {
                 const int sl = (int)(ita & 1);
                 if (lane == 0) mbar_wait(&a1_empty[sl], (uint32_t)(((ita >> 1) & 1) ^ 1), abort_flag);
                 __syncwarp();
@@ -318,7 +298,7 @@ __global__ void __launch_bounds__(F_THREADS, 1)
                         *(uint2 *)(lo + off) = make_uint2(pack_bf16x2(l[0], l[1]), pack_bf16x2(l[2], l[3]));
                     }
                 }
-                if (p == 3) {  // every D0 column of this unit is in registers or shared memory
+                if (j == 3) {  // every D0 column of this unit is in registers or shared memory
                     tc_fence_before();
                     __syncwarp();
                     if (lane == 0) mbar_arrive(d0_empty);
