@@ -250,9 +250,10 @@ def leaf_bytes(desc, m, src_bytes):
 
 def measure_batched(args, count=256, steps=None, warmup=None):
     """Batched persistent launch: ``count`` independent networks of uneven
-    sizes (n 16-28, 2-8 subcircuits, 2-12 cuts, full 2^n outputs each)
-    reconstructed by one tqc_contract_batch launch replayed from a CUDA
-    graph, against contracting them one after the other.  Raw probabilities
+    sizes (n 16-28, 2-8 subcircuits, 2-12 cuts, full 2^n outputs each), with
+    tile configurations from the autotuner, reconstructed by one
+    tqc_contract_batch launch replayed from a CUDA graph, against
+    contracting them one after the other.  Raw probabilities
     (the Gaussian FP32 test tensors can have a total mass near zero)."""
     import torch
     import oracle
@@ -264,7 +265,8 @@ def measure_batched(args, count=256, steps=None, warmup=None):
     hs, plans, outs = [], [], []
     for net in nets:
         h = tqc.Network(net, dtype=tqc.F32)
-        p = tqc.Plan(h, precision=args.precision, flags=tqc.FLAG_NO_RENORM)
+        # tile configurations from the autotuner (its choices are cached by step shape)
+        p = tqc.Plan(h, precision=args.precision, flags=tqc.FLAG_NO_RENORM, autotune=1)
         o = torch.empty(p.out_elems, dtype=torch.float32, device="cuda")
         p.contract(o)
         hs.append(h)

@@ -726,7 +726,10 @@ tqc_status build_batch(Plan *const *plans, void *const *outs, int n, Batch *b) {
             int64_t row_tiles = (int64_t)1 << (sp.mb - bs.a.epi.a_bits);
             int64_t per_item;
             if (sp.klass == KC_UMMA) {
-                bs.bn = sp.nb >= 8 ? 256 : (sp.nb >= 7 ? 128 : 64);
+                // the tile width of the plan's own configuration (the autotuner's
+                // choice when the plan was tuned), run with the direct epilogue
+                const int want = sp.tile == UMMA_128x256_DEEP ? 256 : (sp.tile == UMMA_128x64 ? 64 : 128);
+                bs.bn = std::min(want, sp.nb >= 8 ? 256 : (sp.nb >= 7 ? 128 : 64));
                 const int lbn = bs.bn == 256 ? 8 : (bs.bn == 128 ? 7 : 6);
                 bs.col_tiles = sp.nb >= lbn ? (int64_t)1 << (sp.nb - lbn) : 1;
                 bs.k_blocks = (int)(((int64_t)1 << sp.kb) / (sp.prec == TQC_PREC_TF32 ? 32 : 64));

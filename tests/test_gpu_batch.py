@@ -92,6 +92,29 @@ def test_batch_matches_oracle(mode):
         p.close()
 
 
+def test_batch_autotuned_tiles():
+    """Plans tuned by the autotuner: the batch runs each tensor-core step at
+    the tile width the autotuner chose, with the same results."""
+    nets = uneven_networks()
+    hs, plans, outs, want = [], [], [], []
+    for net in nets:
+        h = tqc.Network(net)
+        p = tqc.Plan(h, precision="auto", autotune=1)
+        o = torch.empty(p.out_elems, dtype=torch.float32, device="cuda")
+        p.contract(o)
+        assert p.describe()["tuned"] == 1
+        hs.append(h)
+        plans.append(p)
+        outs.append(torch.full_like(o, float("nan")))
+        zo = oracle.total_mass(net)
+        want.append((oracle.recon_bin(net) / zo, term_scale(net) / abs(zo)))
+    tqc.contract_batch(plans, outs)
+    tqc.batch_status()
+    check(outs, want, plans)
+    for p in plans:
+        p.close()
+
+
 def test_batch_k_blocked_operands():
     """Plans whose deep steps read K-blocked operands (rows over 64 KB)."""
     nets = [tensors.pseudo_physical_network(14, [(0, 1)] * 8, [list(range(7)), list(range(7, 14))], 3200),
