@@ -89,7 +89,9 @@ enum {
 enum {
     TQC_FLAG_NO_RENORM = 1,      /* skip division by the total mass Z (Z still reported) */
     TQC_FLAG_REUSE = 2,          /* keep intermediates across tqc_contract calls (see there) */
-    TQC_FLAG_NO_FUSE = 4         /* run every step as its own kernel (no fused step pairs) */
+    TQC_FLAG_NO_FUSE = 4,        /* run every step as its own kernel (no fused step pairs) */
+    TQC_FLAG_NO_SMALLK = 8       /* CUDA-core steps with K = 1, 4 or 16 take the general
+                                    64 x 64 .. 128 x 128 tiles instead of the small-K tile */
 };
 
 /*

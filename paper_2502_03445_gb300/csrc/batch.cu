@@ -2,8 +2,8 @@
 // uneven sizes) drained by one persistent kernel from a device work list.
 //
 // Work items, in dependency levels: ingest chunks of every plan's leaf
-// operands, then the tiles of each pairwise step (CUDA-core 64 x 64 tiles or
-// tensor-core 128 x BN tiles).  Every item names at most two counters it
+// operands, then the tiles of each pairwise step (CUDA-core tiles, 64 x 64
+// or the small-K form, or tensor-core 128 x BN tiles).  Every item names at most two counters it
 // waits for (its operands' producers) and one it increments.  CTAs claim
 // items in list order with an atomic counter, so an item only ever waits for
 // items already claimed by running CTAs: no co-residency is needed, and the
@@ -25,6 +25,7 @@
 
 #include "device_common.cuh"
 #include "launch.h"
+#include "smallk.cuh"
 
 struct tqc_plan {
     tqc::Plan p;
@@ -49,6 +50,8 @@ struct alignas(128) BStep {
     StepArgs a;
     int32_t klass, prec, bn, k_blocks, bres;
     int32_t gmode;        // CUDA-core tiles: gather mode of the staged write-out
+    int32_t smallk;       // CUDA-core tiles of the small-K form (smallk.cuh), with
+    int32_t sk_rowmajor, sk_pitch;  // its staging orientation and pitch
     int64_t col_tiles;
     int32_t dep[2];
     int64_t need[2];
@@ -72,6 +75,7 @@ constexpr int G_STAGE = G_BK * (G_PA + G_PB) * 4;
 constexpr int G_TABLES = 2 * G_STAGE + 64 * G_PS * 4;  // the step's write-out tables, copied per item
 constexpr int G_BYTES = G_TABLES + (int)sizeof(EpiTables);
 static_assert(4 * G_BYTES <= RING, "worker buffers alias the ring");
+static_assert(SMALLK_BYTES <= G_TABLES, "a small-K tile fits a worker buffer");
 
 constexpr int SM_MISC = 2048;
 constexpr int SMEM = 1024 + RING + SM_MISC;
@@ -326,9 +330,10 @@ struct Ctl {
 // tcgen05.mma into one of two TMEM accumulators, and the 16 other warps load
 // each accumulator and store it straight to the result layout.  Every stage
 // keeps its own phase bits, so items of different stage sizes restart the
-// ring at stage 0.  A CUDA-core item is a range of 64 x 64 tiles taken by four
-// 4-warp groups; an ingest item a range of leaf elements.  Between items the
-// whole CTA synchronises: the ring and the group buffers share memory.
+// ring at stage 0.  A CUDA-core item is a range of tiles (64 x 64, or the
+// small-K form of smallk.cuh) taken by four 4-warp groups; an ingest item a
+// range of leaf elements.  Between items the whole CTA synchronises: the
+// ring and the group buffers share memory.
 __global__ void __launch_bounds__(BT, 1)
     batch_kernel(const BItem *items, int64_t n_items, const BStep *steps, const EpiTables *tables, const BIngest *ing,
                  unsigned long long *counters, unsigned long long *next, int *err) {
@@ -402,7 +407,12 @@ __global__ void __launch_bounds__(BT, 1)
                 const uint4 *src = (const uint4 *)&tables[item.idx];
                 for (int i = gt; i < (int)(sizeof(EpiTables) / 16); i += 128) ((uint4 *)tb)[i] = src[i];
                 bar_sync(2 + g, 128);
-                simt_range(steps[item.idx], tb, item.tile + g, item.tile + item.count, buf, 2 + g, gt);
+                const BStep &st = steps[item.idx];
+                if (st.smallk)
+                    smallk_dispatch<true>(st.a, tb, st.sk_rowmajor, st.sk_pitch, st.gmode, st.col_tiles, item.tile + g,
+                                    item.tile + item.count, 4, (float *)buf, gt, 2 + g);
+                else
+                    simt_range(st, tb, item.tile + g, item.tile + item.count, buf, 2 + g, gt);
             }
         } else if (run) {
             const BStep &st = steps[item.idx];
@@ -711,7 +721,9 @@ tqc_status build_batch(Plan *const *plans, void *const *outs, int n, Batch *b) {
             std::memset((void *)&bs, 0, sizeof bs);
             bs.klass = sp.klass;
             bs.prec = sp.prec;
-            TileShape ts = sp.klass == KC_UMMA ? TileShape{7, 6} : TileShape{6, 6};
+            const bool smallk = sp.klass != KC_UMMA && sp.tile == SIMT_SMALLK;
+            TileShape ts = sp.klass == KC_UMMA ? TileShape{7, 6}
+                                               : (smallk ? smallk_tile(sp.mb, sp.nb, sp.kb) : TileShape{6, 6});
             bs.a = exec_step_args(p, sp, ts);
             const TensorPlan &tc = p.tensors[sp.c];
             bs.a.epi.zinfo = p.d_zinfo;
@@ -741,6 +753,13 @@ tqc_status build_batch(Plan *const *plans, void *const *outs, int n, Batch *b) {
                 bs.bn = 64;
                 bs.col_tiles = (int64_t)1 << (sp.nb - bs.a.epi.b_bits);
                 bs.gmode = gather_mode(bs.a.epi.lowCc);
+                if (smallk) {
+                    const StagePick pk = pick_staging(bs.a.epi.lowRc, bs.a.epi.lowCc);
+                    bs.smallk = 1;
+                    bs.sk_rowmajor = pk.rowmajor;
+                    bs.sk_pitch = pk.rowmajor ? (1 << bs.a.epi.b_bits) + 4 : (1 << bs.a.epi.a_bits) + 4;
+                    bs.gmode = pk.gmode;
+                }
             }
             const int64_t n_tiles = row_tiles * bs.col_tiles;
             // items of 16 tiles, larger for large steps (fewer pipeline drains),
@@ -758,7 +777,9 @@ tqc_status build_batch(Plan *const *plans, void *const *outs, int n, Batch *b) {
             const int lvl = 1 + std::max(level_of[sp.a], level_of[sp.b]);
             level_of[sp.c] = lvl;
             EpiTables tb;
-            host_tables(&tb, bs.a.epi, true, 68);  // staged write-out of the 64 x 64 CUDA-core tiles
+            // staged write-out of the CUDA-core tiles (64 x 64 row-major, or the small-K form's)
+            if (bs.smallk) host_tables(&tb, bs.a.epi, bs.sk_rowmajor != 0, bs.sk_pitch);
+            else host_tables(&tb, bs.a.epi, true, 68);
             const int si = (int)steps.size();
             steps.push_back(bs);
             tables.push_back(tb);

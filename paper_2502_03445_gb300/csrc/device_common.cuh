@@ -220,54 +220,6 @@ __host__ __device__ inline StagePick pick_staging(uint32_t lowRc, uint32_t lowCc
     return p;
 }
 
-// Write the staged tile (E = 2^(a+b) elements) to its destination.
-__device__ __forceinline__ void epi_readout(const EpiTables *tb, const float *stg, const EpiParams &e,
-                                            uint64_t base, int E, int tid, int nthreads, int gmode) {
-    const double s = (e.mode == EPI_OUT_F32 || e.mode == EPI_OUT_F64) ? e.zinfo[1] : 1.0;
-    if (e.L >= 2) {
-#pragma unroll 4
-        for (int t = tid * 4; t < E; t += nthreads * 4) {
-            const uint32_t sh = tb->s_hi[t >> 7];
-            const int tl = t & 127;
-            const uint32_t s0 = sh + tb->s_lo[tl];
-            float v[4];
-            if (gmode == G_VEC4) {
-                const float4 q = *(const float4 *)(stg + s0);
-                v[0] = q.x;
-                v[1] = q.y;
-                v[2] = q.z;
-                v[3] = q.w;
-            } else if (gmode == G_PAIR01) {
-                const float2 a = *(const float2 *)(stg + s0);
-                const float2 b = *(const float2 *)(stg + sh + tb->s_lo[tl + 2]);
-                v[0] = a.x;
-                v[1] = a.y;
-                v[2] = b.x;
-                v[3] = b.y;
-            } else if (gmode == G_PAIR02) {
-                const float2 a = *(const float2 *)(stg + s0);
-                const float2 b = *(const float2 *)(stg + sh + tb->s_lo[tl + 1]);
-                v[0] = a.x;
-                v[1] = b.x;
-                v[2] = a.y;
-                v[3] = b.y;
-            } else {
-                v[0] = stg[s0];
-                v[1] = stg[sh + tb->s_lo[tl + 1]];
-                v[2] = stg[sh + tb->s_lo[tl + 2]];
-                v[3] = stg[sh + tb->s_lo[tl + 3]];
-            }
-            store_run_f32(e, base + tb->g_hi[t >> 7] + tb->g_lo[tl], v, 4, s);
-        }
-    } else {
-        for (int t = tid; t < E; t += nthreads) {
-            float v = stg[tb->s_hi[t >> 7] + tb->s_lo[t & 127]];
-            store_run_f32(e, base + tb->g_hi[t >> 7] + tb->g_lo[t & 127], &v, 1, s);
-        }
-    }
-}
-
-
 // Store VW (1, 2 or 4) consecutive values of an epilogue in output mode MODE
 // (the compile-time twin of store_run_f32, for loops that dispatch the mode
 // once instead of per store); sf / sd: the EPI_OUT_* scale in FP32 / FP64.
@@ -329,6 +281,84 @@ __device__ __forceinline__ void store_vals(const EpiParams &e, uint64_t off, con
                 for (int i = 0; i < VW; i += 2) ((double2 *)o)[i / 2] = make_double2(w[i], w[i + 1]);
             }
         }
+    }
+}
+
+// Write the staged tile (E = 2^(a+b) elements) to its destination.
+// nthreads is a multiple of 32: a thread's t advances by a multiple of 128,
+// so its low table entries (t & 127) are read once, not once per run (the
+// lanes of a warp read them at a stride of four entries: bank conflicts).
+// The output mode is dispatched once per tile (MODE >= 0), or per store
+// (MODE = -1: fewer registers, for kernels with a tight budget).
+template <int MODE>
+__device__ __forceinline__ void epi_readout_m(const EpiTables *tb, const float *stg, const EpiParams &e,
+                                              uint64_t base, int E, int tid, int nthreads, int gmode) {
+    const int mode = MODE >= 0 ? MODE : e.mode;
+    const double sd = (mode == EPI_OUT_F32 || mode == EPI_OUT_F64) ? e.zinfo[1] : 1.0;
+    const float sf = (float)sd;
+    if (e.L >= 2) {
+        const int tl = (tid * 4) & 127;
+        const uint32_t l0 = tb->s_lo[tl], l1 = tb->s_lo[tl + 1], l2 = tb->s_lo[tl + 2], l3 = tb->s_lo[tl + 3];
+        const uint64_t gbase = base + tb->g_lo[tl];
+#pragma unroll 4
+        for (int t = tid * 4; t < E; t += nthreads * 4) {
+            const float *sp = stg + tb->s_hi[t >> 7];
+            float v[4];
+            if (gmode == G_VEC4) {
+                const float4 q = *(const float4 *)(sp + l0);
+                v[0] = q.x;
+                v[1] = q.y;
+                v[2] = q.z;
+                v[3] = q.w;
+            } else if (gmode == G_PAIR01) {
+                const float2 a = *(const float2 *)(sp + l0);
+                const float2 b = *(const float2 *)(sp + l2);
+                v[0] = a.x;
+                v[1] = a.y;
+                v[2] = b.x;
+                v[3] = b.y;
+            } else if (gmode == G_PAIR02) {
+                const float2 a = *(const float2 *)(sp + l0);
+                const float2 b = *(const float2 *)(sp + l1);
+                v[0] = a.x;
+                v[1] = b.x;
+                v[2] = a.y;
+                v[3] = b.y;
+            } else {
+                v[0] = sp[l0];
+                v[1] = sp[l1];
+                v[2] = sp[l2];
+                v[3] = sp[l3];
+            }
+            if constexpr (MODE >= 0) store_vals<MODE, 4>(e, gbase + tb->g_hi[t >> 7], v, sf, sd);
+            else store_run_f32(e, gbase + tb->g_hi[t >> 7], v, 4, sd);
+        }
+    } else {
+        for (int t = tid; t < E; t += nthreads) {
+            float v = stg[tb->s_hi[t >> 7] + tb->s_lo[t & 127]];
+            if constexpr (MODE >= 0) store_vals<MODE, 1>(e, base + tb->g_hi[t >> 7] + tb->g_lo[t & 127], &v, sf, sd);
+            else store_run_f32(e, base + tb->g_hi[t >> 7] + tb->g_lo[t & 127], &v, 1, sd);
+        }
+    }
+}
+
+__device__ __forceinline__ void epi_readout_rt(const EpiTables *tb, const float *stg, const EpiParams &e,
+                                               uint64_t base, int E, int tid, int nthreads, int gmode) {
+    epi_readout_m<-1>(tb, stg, e, base, E, tid, nthreads, gmode);
+}
+
+__device__ __forceinline__ void epi_readout(const EpiTables *tb, const float *stg, const EpiParams &e,
+                                            uint64_t base, int E, int tid, int nthreads, int gmode) {
+    switch (e.mode) {
+        case EPI_F32: epi_readout_m<EPI_F32>(tb, stg, e, base, E, tid, nthreads, gmode); break;
+        case EPI_TF32: epi_readout_m<EPI_TF32>(tb, stg, e, base, E, tid, nthreads, gmode); break;
+        case EPI_BF16: epi_readout_m<EPI_BF16>(tb, stg, e, base, E, tid, nthreads, gmode); break;
+        case EPI_BF16X2: epi_readout_m<EPI_BF16X2>(tb, stg, e, base, E, tid, nthreads, gmode); break;
+        case EPI_F64_SET: epi_readout_m<EPI_F64_SET>(tb, stg, e, base, E, tid, nthreads, gmode); break;
+        case EPI_F64_ADD: epi_readout_m<EPI_F64_ADD>(tb, stg, e, base, E, tid, nthreads, gmode); break;
+        case EPI_OUT_F32: epi_readout_m<EPI_OUT_F32>(tb, stg, e, base, E, tid, nthreads, gmode); break;
+        case EPI_OUT_F64: epi_readout_m<EPI_OUT_F64>(tb, stg, e, base, E, tid, nthreads, gmode); break;
+        default: break;
     }
 }
 

@@ -128,7 +128,10 @@ tqc_status launch_step(const Plan &p, const StepPlan &st, StepArgs &a, int *d_er
     return TQC_OK;
 }
 
-TileShape tile_of(const StepPlan &st) { return st.klass == KC_UMMA ? umma_tile(st.tile) : simt_tile(st.tile); }
+TileShape tile_of(const StepPlan &st) {
+    if (st.klass == KC_UMMA) return umma_tile(st.tile);
+    return st.tile == SIMT_SMALLK ? smallk_tile(st.mb, st.nb, st.kb) : simt_tile(st.tile);
+}
 
 // ---------------------------------------------------------------- autotuner
 // For every step, time each tile configuration that fits the step on the
@@ -136,17 +139,17 @@ TileShape tile_of(const StepPlan &st) { return st.klass == KC_UMMA ? umma_tile(s
 // and keep the fastest.  Results are cached process-wide by the step's
 // shape and epilogue pattern, so equal steps of other plans reuse them.
 struct TuneKey {
-    int klass, prec, mb, nb, kb, mode;
+    int klass, prec, mb, nb, kb, mode, smallk;
     uint64_t maskR, maskC;
     bool operator<(const TuneKey &o) const {
-        return std::tie(klass, prec, mb, nb, kb, mode, maskR, maskC) <
-               std::tie(o.klass, o.prec, o.mb, o.nb, o.kb, o.mode, o.maskR, o.maskC);
+        return std::tie(klass, prec, mb, nb, kb, mode, smallk, maskR, maskC) <
+               std::tie(o.klass, o.prec, o.mb, o.nb, o.kb, o.mode, o.smallk, o.maskR, o.maskC);
     }
 };
 std::map<TuneKey, int> g_tune_cache;
 std::mutex g_tune_mu;
 
-std::vector<int> tile_candidates(const StepPlan &st) {
+std::vector<int> tile_candidates(const StepPlan &st, bool smallk) {
     std::vector<int> c;
     if (st.klass == KC_UMMA) {
         if (st.nb >= 7) c.push_back(UMMA_128x128);
@@ -154,6 +157,7 @@ std::vector<int> tile_candidates(const StepPlan &st) {
         if (st.mb >= 7 && st.nb >= 7) c.push_back(UMMA_128x128_DEEP);
         if (st.mb >= 7 && st.nb >= 8) c.push_back(UMMA_128x256_DEEP);
     } else {
+        if (smallk && smallk_ok(st.mb, st.nb, st.kb, st.kblk)) c.push_back(SIMT_SMALLK);
         c.push_back(SIMT_64x64);
         if (st.mb >= 7 && st.nb >= 6) c.push_back(SIMT_128x64);
         if (st.mb >= 7 && st.nb >= 7) c.push_back(SIMT_128x128);
@@ -203,7 +207,9 @@ double direct_store_efficiency(const EpiParams &e, int esize) {
 //    expansion of a final step), with 128 x 256 tiles when N allows (grid30's
 //    final step: 0.92 ms against 1.50 ms staged), else 128 x 128 (grid30's
 //    step 1, N = 128: 0.48 ms against 0.56 ms, the autotuner's choice).
-int default_step_tile(const StepPlan &st, int out_esize) {
+// CUDA-core steps with K of 1, 4 or 16 take the small-K tile (unless
+// `smallk` is false).
+int default_step_tile(const StepPlan &st, int out_esize, bool smallk) {
     if (st.klass == KC_UMMA) {
         const bool big = st.mb >= 7 && st.nb >= 7;
         const bool deep = big && st.kb >= DEEP_MIN_LOG2_K;
@@ -215,6 +221,7 @@ int default_step_tile(const StepPlan &st, int out_esize) {
         }
         return st.nb >= 7 ? UMMA_128x128 : UMMA_128x64;
     }
+    if (smallk && smallk_ok(st.mb, st.nb, st.kb, st.kblk)) return SIMT_SMALLK;
     return (st.mb >= 7 && st.nb >= 7) ? SIMT_128x128 : (st.mb >= 7 && st.nb >= 6 ? SIMT_128x64 : SIMT_64x64);
 }
 
@@ -308,7 +315,8 @@ tqc_status exec_autotune(Plan *p, void *d_out, int out_dtype, cudaStream_t s) {
         const TensorPlan &tc = p->tensors[sp.c];
         int mode = sp.final ? (sliced ? EPI_F64_SET : (out_dtype == TQC_F64 ? EPI_OUT_F64 : EPI_OUT_F32))
                             : epi_mode_of(tc.storage);
-        TuneKey key{sp.klass, sp.prec, sp.mb, sp.nb, sp.kb, mode, sp.maskR, sp.maskC};
+        const bool smallk = !(p->flags & TQC_FLAG_NO_SMALLK);
+        TuneKey key{sp.klass, sp.prec, sp.mb, sp.nb, sp.kb, mode, smallk ? 1 : 0, sp.maskR, sp.maskC};
         {
             std::lock_guard<std::mutex> lk(g_tune_mu);
             auto it = g_tune_cache.find(key);
@@ -319,7 +327,7 @@ tqc_status exec_autotune(Plan *p, void *d_out, int out_dtype, cudaStream_t s) {
         }
         float best = 1e30f;
         int best_tile = sp.tile;
-        for (int cand : tile_candidates(sp)) {
+        for (int cand : tile_candidates(sp, smallk)) {
             StepPlan trial = sp;
             trial.tile = cand;
             StepArgs a = step_args(*p, p->tensors, trial, p->d_ws, tile_of(trial));
@@ -389,7 +397,7 @@ tqc_status exec_prepare(Plan *p) {
     }
     // tile choice without autotuning: big tiles for big steps
     for (auto &st : p->steps) {
-        st.tile = default_step_tile(st, step_out_esize(*p, st));
+        st.tile = default_step_tile(st, step_out_esize(*p, st), !(p->flags & TQC_FLAG_NO_SMALLK));
     }
     tqc_status kst = update_ksplit(p);
     if (kst != TQC_OK) {
@@ -486,7 +494,7 @@ tqc_status exec_run(Plan &pl, const ExecCtx &c, const uint8_t *fixed_bits, void 
     auto step_of = [&](const StepPlan &sp) {
         StepPlan x = sp;
         if (c.default_tiles) {
-            x.tile = default_step_tile(sp, step_out_esize(*p, sp));
+            x.tile = default_step_tile(sp, step_out_esize(*p, sp), !(p->flags & TQC_FLAG_NO_SMALLK));
             x.ksplit = 1;
         }
         return x;

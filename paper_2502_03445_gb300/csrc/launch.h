@@ -7,14 +7,20 @@
 
 namespace tqc {
 
-// CUDA-core step tiles (FP32), chosen by the autotuner
-enum SimtCfg { SIMT_64x64 = 0, SIMT_128x128 = 1, SIMT_128x64 = 2, SIMT_N_CFG = 3 };
+// CUDA-core step tiles (FP32), chosen by the autotuner; SIMT_SMALLK: the
+// write-out-shaped tile of steps with K = 1, 4 or 16 (smallk.cuh)
+enum SimtCfg { SIMT_64x64 = 0, SIMT_128x128 = 1, SIMT_128x64 = 2, SIMT_SMALLK = 3, SIMT_N_CFG = 4 };
 
 struct TileShape {
     int log_bm, log_bn;
 };
 
 TileShape simt_tile(int cfg);
+// Whether a CUDA-core step can take SIMT_SMALLK (K of 1, 4 or 16 over plain
+// row-major FP32 operands, at least 4 rows, 4 columns and 128 results), and
+// its tile shape.
+bool smallk_ok(int mb, int nb, int kb, bool kblk);
+TileShape smallk_tile(int mb, int nb, int kb);
 TileShape simt_f64_tile();
 int sm_count();
 
@@ -57,7 +63,7 @@ constexpr int DEEP_MIN_LOG2_K = 12;
 // measured 6% faster at K = 2^14, slower at K = 2^10 (short loops) and at
 // K = 2^18 (rows of 512 KB: twice the boxes per byte, each across pages).
 constexpr int SW64_MIN_LOG2_K = 12;
-int default_step_tile(const StepPlan &st, int out_esize);
+int default_step_tile(const StepPlan &st, int out_esize, bool smallk = true);
 // K splits of a final tensor-core step with too few tiles to fill the GPU
 // evenly (1 = no split); max_part_bytes caps the FP32 partials it stores.
 int step_ksplit(const StepPlan &st, int64_t out_elems, int64_t max_part_bytes);

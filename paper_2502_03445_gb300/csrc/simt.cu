@@ -14,6 +14,7 @@
 
 #include "device_common.cuh"
 #include "launch.h"
+#include "smallk.cuh"
 
 namespace tqc {
 
@@ -91,6 +92,18 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
     }
 }
 
+
+// Small-K step (smallk.cuh): one 128-thread CTA per tile slot, the staging
+// tables built once per CTA.
+__global__ void __launch_bounds__(128) simt_smallk_f32(StepArgs args, int64_t n_tiles, int64_t col_tiles, int rowmajor,
+                                                       int pitch, int gmode) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    EpiTables *tb = (EpiTables *)smem_raw;
+    float *buf = (float *)(smem_raw + sizeof(EpiTables));
+    epi_tables_init(tb, args.epi, rowmajor != 0, pitch, threadIdx.x, 128);
+    __syncthreads();
+    smallk_dispatch<false>(args, tb, rowmajor, pitch, gmode, col_tiles, blockIdx.x, n_tiles, gridDim.x, buf, threadIdx.x, 1);
+}
 
 // FP64 twin for the scalar total-mass network (small; one config).
 template <int BM, int BN, int TM, int TN>
@@ -281,8 +294,57 @@ TileShape simt_tile(int cfg) {
 
 TileShape simt_f64_tile() { return {5, 5}; }
 
+bool smallk_ok(int mb, int nb, int kb, bool kblk) {
+    return (kb == 0 || kb == 2 || kb == 4) && !kblk && mb >= 2 && nb >= 2 && mb + nb >= 7;
+}
+
+// Start from 64 x 64, grow the side the step still has until the tile holds
+// 2^12 results, then shrink the larger side until operands and staging (in
+// either orientation) fit SMALLK_BYTES.
+TileShape smallk_tile(int mb, int nb, int kb) {
+    int a = std::min(mb, 6), b = std::min(nb, 6);
+    while (a + b < 12 && (a < mb || b < nb)) {
+        if (a < mb && (a <= b || b >= nb)) ++a;
+        else ++b;
+    }
+    auto fits = [&](int x, int y) {
+        return smallk_op_bytes(x, y, kb) <= SMALLK_BYTES &&
+               std::max(smallk_stage_bytes(x, y, true), smallk_stage_bytes(x, y, false)) <= SMALLK_BYTES;
+    };
+    while (!fits(a, b) && (a > 2 || b > 2)) {
+        if (a >= b && a > 2) --a;
+        else --b;
+    }
+    return TileShape{a, b};
+}
+
+cudaError_t launch_smallk(const StepArgs &a, cudaStream_t s) {
+    const EpiParams &e = a.epi;
+    if (!smallk_ok(a.mb, a.nb, a.kb, a.kblk != 0) || e.a_bits < 2 || e.b_bits < 2 || a.ksplit != 1)
+        return cudaErrorInvalidValue;
+    const StagePick pk = pick_staging(e.lowRc, e.lowCc);
+    const int pitch = pk.rowmajor ? (1 << e.b_bits) + 4 : (1 << e.a_bits) + 4;
+    const int bytes = std::max(smallk_op_bytes(e.a_bits, e.b_bits, a.kb),
+                               smallk_stage_bytes(e.a_bits, e.b_bits, pk.rowmajor != 0));
+    if (bytes > SMALLK_BYTES) return cudaErrorInvalidValue;
+    const size_t smem = sizeof(EpiTables) + (size_t)bytes;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t err = cudaFuncSetAttribute(simt_smallk_f32, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)(sizeof(EpiTables) + SMALLK_BYTES));
+        if (err != cudaSuccess) return err;
+        attr = true;
+    }
+    const int64_t col_tiles = 1ll << (a.nb - e.b_bits);
+    const int64_t n_tiles = (1ll << (a.mb - e.a_bits)) * col_tiles;
+    const int64_t grid = std::min<int64_t>(n_tiles, (int64_t)sm_count() * 16);
+    simt_smallk_f32<<<(unsigned)grid, 128, smem, s>>>(a, n_tiles, col_tiles, pk.rowmajor, pitch, pk.gmode);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_simt_step(int cfg, const StepArgs &a, cudaStream_t s) {
     switch (cfg) {
+        case SIMT_SMALLK: return launch_smallk(a, s);
         case SIMT_128x128: return launch_cfg<128, 128, 8, 8>(a, s);
         case SIMT_128x64: return launch_cfg<128, 64, 8, 4>(a, s);
         default: return launch_cfg<64, 64, 4, 4>(a, s);

@@ -1,0 +1,200 @@
+// One tile of a small-K CUDA-core step (K = 1, 4 or 16: one subcircuit pair
+// sharing at most two cut edges), computed by a group of 128 threads.
+//
+// Such a step moves far more bytes than it multiplies: a result element
+// costs K multiply-adds and 4 bytes of HBM writes, so the tile is shaped for
+// the write-out, not for arithmetic reuse.  It spans a + b = 12 result bits
+// (4096 elements; fewer when the step is smaller or the operands would not
+// fit the buffer): the lowest a row bits and lowest b column bits of the
+// result layout, so that the rows (and columns) it reads are contiguous
+// operand memory, loaded with 16-byte loads and stored transposed ([k][row],
+// [k][col]) in shared memory.  Every thread then forms 4 x 8 (or 8 x 4)
+// results as outer products of float4 quads, the tile is staged in the
+// orientation that makes the destination-order gather conflict-free, and
+// the staged tile is written with runs of consecutive addresses
+// (epi_readout).  The staging buffer aliases the operand buffer.
+#pragma once
+
+#include "device_common.cuh"
+#include "launch.h"
+
+namespace tqc {
+
+// Shared memory a small-K tile uses (operands and staging alias).
+constexpr int SMALLK_BYTES = 34816;
+
+__host__ __device__ inline int smallk_op_bytes(int a, int b, int kb) {
+    return (1 << kb) * ((1 << a) + 4 + (1 << b) + 4) * 4;
+}
+__host__ __device__ inline int smallk_stage_bytes(int a, int b, bool rowmajor) {
+    return rowmajor ? (1 << a) * ((1 << b) + 4) * 4 : (1 << b) * ((1 << a) + 4) * 4;
+}
+
+__device__ __forceinline__ void sk_bar(int id) { asm volatile("bar.sync %0, 128;" ::"r"(id) : "memory"); }
+
+// Tile (rt, ct) of the step, whose results start at element `base` of the
+// result layout: KB = log2 K; QM x QN float4 quads per thread
+// (QM = 1, QN = 2 when the tile has at least 8 columns, else 2 x 1).  gt: the
+// thread's index in the group, bid: the group's named barrier.  rowmajor /
+// pitch / gmode: the staging orientation and the gather mode the tables
+// `tb` were built for.
+template <int KB, int QM, bool LEAN>
+__device__ __forceinline__ void smallk_tile_run(const StepArgs &sa, const EpiTables *tb, int rowmajor, int pitch,
+                                                int gmode, int64_t rt, int64_t ct, uint64_t base, float *buf, int gt,
+                                                int bid) {
+    constexpr int K = 1 << KB;
+    constexpr int QN = 3 - QM;
+    const EpiParams &e = sa.epi;
+    const int a = e.a_bits, b = e.b_bits;
+    const int Me = 1 << a, Ne = 1 << b;
+    const int PA = Me + 4, PB = Ne + 4;
+    float *As = buf, *Bs = buf + K * PA;
+    const float *A = (const float *)sa.A + (rt << a) * (int64_t)K;
+    const float *B = (const float *)sa.B + (ct << b) * (int64_t)K;
+    // operands: rows [rt 2^a, (rt + 1) 2^a) of A and the tile's columns of B,
+    // contiguous in memory; transposed to [k][row] / [k][col]
+    if constexpr (K == 1) {
+        for (int f = gt; f < Me / 4; f += 128) *(float4 *)&As[4 * f] = *(const float4 *)(A + 4 * f);
+        for (int f = gt; f < Ne / 4; f += 128) *(float4 *)&Bs[4 * f] = *(const float4 *)(B + 4 * f);
+    } else {
+        constexpr int KQ = K / 4, LKQ = KB - 2;
+        for (int f = gt; f < Me * KQ; f += 128) {
+            const float4 v = *(const float4 *)(A + 4 * (int64_t)f);
+            const int r = f >> LKQ, k = (f & (KQ - 1)) * 4;
+            As[k * PA + r] = v.x;
+            As[(k + 1) * PA + r] = v.y;
+            As[(k + 2) * PA + r] = v.z;
+            As[(k + 3) * PA + r] = v.w;
+        }
+        for (int f = gt; f < Ne * KQ; f += 128) {
+            const float4 v = *(const float4 *)(B + 4 * (int64_t)f);
+            const int c = f >> LKQ, k = (f & (KQ - 1)) * 4;
+            Bs[k * PB + c] = v.x;
+            Bs[(k + 1) * PB + c] = v.y;
+            Bs[(k + 2) * PB + c] = v.z;
+            Bs[(k + 3) * PB + c] = v.w;
+        }
+    }
+    sk_bar(bid);
+    // thread (tx, ty) owns row quads ty + Y u and column quads tx + X v; the
+    // lanes of a warp run along the staging buffer's contiguous dimension
+    // (columns when it is row-major), so that its float4 writes are
+    // conflict-free
+    const int X = (Ne >> 2) / QN, Y = (Me >> 2) / QM;
+    const int tx = rowmajor ? gt % X : gt / Y, ty = rowmajor ? gt / X : gt % Y;
+    const bool active = gt < X * Y;
+    float acc[4 * QM][4 * QN];
+#pragma unroll
+    for (int u = 0; u < 4 * QM; ++u)
+#pragma unroll
+        for (int v = 0; v < 4 * QN; ++v) acc[u][v] = 0.f;
+    if (active) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            float4 av[QM], bv[QN];
+#pragma unroll
+            for (int u = 0; u < QM; ++u) av[u] = *(const float4 *)&As[k * PA + 4 * (ty + Y * u)];
+#pragma unroll
+            for (int v = 0; v < QN; ++v) bv[v] = *(const float4 *)&Bs[k * PB + 4 * (tx + X * v)];
+#pragma unroll
+            for (int u = 0; u < QM; ++u) {
+                const float ar[4] = {av[u].x, av[u].y, av[u].z, av[u].w};
+#pragma unroll
+                for (int v = 0; v < QN; ++v) {
+                    const float br[4] = {bv[v].x, bv[v].y, bv[v].z, bv[v].w};
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) acc[4 * u + i][4 * v + j] = fmaf(ar[i], br[j], acc[4 * u + i][4 * v + j]);
+                }
+            }
+        }
+    }
+    sk_bar(bid);  // operands read: the staging buffer aliases them
+    float *stg = buf;
+    if (active) {
+#pragma unroll
+        for (int u = 0; u < QM; ++u)
+#pragma unroll
+            for (int v = 0; v < QN; ++v) {
+                const int r0 = 4 * (ty + Y * u), c0 = 4 * (tx + X * v);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    if (rowmajor)
+                        *(float4 *)&stg[(r0 + i) * pitch + c0] =
+                            make_float4(acc[4 * u + i][4 * v], acc[4 * u + i][4 * v + 1], acc[4 * u + i][4 * v + 2],
+                                        acc[4 * u + i][4 * v + 3]);
+                    else
+                        *(float4 *)&stg[(c0 + i) * pitch + r0] =
+                            make_float4(acc[4 * u][4 * v + i], acc[4 * u + 1][4 * v + i], acc[4 * u + 2][4 * v + i],
+                                        acc[4 * u + 3][4 * v + i]);
+                }
+            }
+    }
+    sk_bar(bid);
+    if constexpr (LEAN) epi_readout_rt(tb, stg, e, base, Me * Ne, gt, 128, gmode);
+    else epi_readout(tb, stg, e, base, Me * Ne, gt, 128, gmode);
+    sk_bar(bid);  // the next tile's operands overwrite the staging buffer
+}
+
+// Tiles t0, t0 + stride, ... < t_end of a small-K step (col_tiles: a power
+// of two).  The tile's row / column block and its base element advance by
+// masked additions instead of a division and two bit deposits per tile:
+// with every bit outside mask M set, pdep(x, M) + pdep(d, M) carries across
+// the gaps, so ((P | ~M) + pdep(d, M)) & M = pdep(x + d, M) (modulo the
+// mask's width: the column block wraps and carries into the row block).
+// LEAN (for a caller with a tight register budget, which saves its live
+// registers once per call of this non-inlined loop): the tile base is
+// deposited per tile and the output mode dispatched per store, which keep
+// fewer values live.
+template <int KB, int QM, bool LEAN>
+__device__ __noinline__ void smallk_tiles(const StepArgs &sa, const EpiTables *tb, int rowmajor, int pitch, int gmode,
+                                          int64_t col_tiles, int64_t t0, int64_t t_end, int64_t stride, float *buf,
+                                          int gt, int bid) {
+    if (t0 >= t_end) return;
+    const EpiParams &e = sa.epi;
+    const int lct = __ffsll((long long)col_tiles) - 1;
+    const int64_t cmask = col_tiles - 1;
+    if constexpr (LEAN) {
+        for (int64_t t = t0; t < t_end; t += stride) {
+            const int64_t r = t >> lct, c = t & cmask;
+            smallk_tile_run<KB, QM, true>(sa, tb, rowmajor, pitch, gmode, r, c, tile_base(e, r, c), buf, gt, bid);
+        }
+        return;
+    }
+    const int64_t sc = stride & cmask, sr = stride >> lct;
+    int64_t rt = t0 >> lct, ct = t0 & cmask;
+    uint64_t pr = pdep64((uint64_t)rt, e.highR), pc = pdep64((uint64_t)ct, e.highC);
+    const uint64_t dc = pdep64((uint64_t)sc, e.highC);
+    const uint64_t dr0 = pdep64((uint64_t)sr, e.highR), dr1 = pdep64((uint64_t)sr + 1, e.highR);
+    for (int64_t t = t0; t < t_end; t += stride) {
+        smallk_tile_run<KB, QM, false>(sa, tb, rowmajor, pitch, gmode, rt, ct, pr | pc, buf, gt, bid);
+        const int64_t c2 = ct + sc;
+        const int carry = (int)(c2 >> lct);
+        ct = c2 & cmask;
+        rt += sr + carry;
+        pc = ((pc | ~e.highC) + dc) & e.highC;
+        pr = ((pr | ~e.highR) + (carry ? dr1 : dr0)) & e.highR;
+    }
+}
+
+template <bool LEAN>
+__device__ __forceinline__ void smallk_dispatch(const StepArgs &sa, const EpiTables *tb, int rowmajor, int pitch,
+                                                int gmode, int64_t col_tiles, int64_t t0, int64_t t_end,
+                                                int64_t stride, float *buf, int gt, int bid) {
+    const bool wide = sa.epi.b_bits >= 3;
+#define TQC_SMALLK_CASE(KBV)                                                                                      \
+    if (sa.kb == KBV) {                                                                                           \
+        if (wide)                                                                                                 \
+            smallk_tiles<KBV, 1, LEAN>(sa, tb, rowmajor, pitch, gmode, col_tiles, t0, t_end, stride, buf, gt, bid); \
+        else                                                                                                      \
+            smallk_tiles<KBV, 2, LEAN>(sa, tb, rowmajor, pitch, gmode, col_tiles, t0, t_end, stride, buf, gt, bid); \
+        return;                                                                                                   \
+    }
+    TQC_SMALLK_CASE(0)
+    TQC_SMALLK_CASE(2)
+    TQC_SMALLK_CASE(4)
+#undef TQC_SMALLK_CASE
+}
+
+}  // namespace tqc

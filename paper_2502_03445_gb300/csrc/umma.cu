@@ -480,7 +480,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     store_run_f32(e, base + r_g[it], v, 4, sc);
                 }
             } else {
-                epi_readout(tb, cur, e, base, E, etid, EPI_THREADS, P.gmode);
+                epi_readout_rt(tb, cur, e, base, E, etid, EPI_THREADS, P.gmode);
             }
             stop = epi_barrier_or(EPI_THREADS, *abort_flag != 0);
         }

@@ -25,6 +25,7 @@ PLANNER_GREEDY, PLANNER_EXHAUSTIVE, PLANNER_LEARNED, PLANNER_AUTO = range(4)
 FLAG_NO_RENORM = 1
 FLAG_REUSE = 2
 FLAG_NO_FUSE = 4
+FLAG_NO_SMALLK = 8
 PREC_NAMES = {"fp32": PREC_FP32, "tf32": PREC_TF32, "bf16": PREC_BF16, "bf16x3": PREC_BF16X3, "auto": PREC_AUTO}
 
 # every symbol include/tqc.h declares
