@@ -289,10 +289,13 @@ __device__ __forceinline__ void store_vals(const EpiParams &e, uint64_t off, con
 // so its low table entries (t & 127) are read once, not once per run (the
 // lanes of a warp read them at a stride of four entries: bank conflicts).
 // The output mode is dispatched once per tile (MODE >= 0), or per store
-// (MODE = -1: fewer registers, for kernels with a tight budget).
+// (MODE = -1: fewer registers, for kernels with a tight budget).  The tables
+// and the staged tile are in shared memory.
 template <int MODE>
 __device__ __forceinline__ void epi_readout_m(const EpiTables *tb, const float *stg, const EpiParams &e,
                                               uint64_t base, int E, int tid, int nthreads, int gmode) {
+    __builtin_assume(__isShared(tb));
+    __builtin_assume(__isShared(stg));
     const int mode = MODE >= 0 ? MODE : e.mode;
     const double sd = (mode == EPI_OUT_F32 || mode == EPI_OUT_F64) ? e.zinfo[1] : 1.0;
     const float sf = (float)sd;

@@ -95,7 +95,7 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
 
 // Small-K step (smallk.cuh): one 128-thread CTA per tile slot, the staging
 // tables built once per CTA.
-__global__ void __launch_bounds__(128) simt_smallk_f32(StepArgs args, int64_t n_tiles, int64_t col_tiles, int rowmajor,
+__global__ void __launch_bounds__(128, 8) simt_smallk_f32(StepArgs args, int64_t n_tiles, int64_t col_tiles, int rowmajor,
                                                        int pitch, int gmode) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     EpiTables *tb = (EpiTables *)smem_raw;

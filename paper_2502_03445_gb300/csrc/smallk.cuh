@@ -32,168 +32,193 @@ __host__ __device__ inline int smallk_stage_bytes(int a, int b, bool rowmajor) {
 
 __device__ __forceinline__ void sk_bar(int id) { asm volatile("bar.sync %0, 128;" ::"r"(id) : "memory"); }
 
-// Tile (rt, ct) of the step, whose results start at element `base` of the
-// result layout: KB = log2 K; QM x QN float4 quads per thread
-// (QM = 1, QN = 2 when the tile has at least 8 columns, else 2 x 1).  gt: the
-// thread's index in the group, bid: the group's named barrier.  rowmajor /
-// pitch / gmode: the staging orientation and the gather mode the tables
-// `tb` were built for.
-template <int KB, int QM, bool LEAN>
-__device__ __forceinline__ void smallk_tile_run(const StepArgs &sa, const EpiTables *tb, int rowmajor, int pitch,
-                                                int gmode, int64_t rt, int64_t ct, uint64_t base, float *buf, int gt,
-                                                int bid) {
+// Tiles t0, t0 + stride, ... < t_end of a small-K step (col_tiles: a power
+// of two).  KB = log2 K; QM x QN float4 quads per thread (QM = 1, QN = 2 when
+// the tile has at least 8 columns, else 2 x 1); RM: the staging buffer is
+// row-major.  gt: the thread's index in the group, bid: the group's named
+// barrier; pitch / gmode: the staging pitch and gather mode the tables `tb`
+// were built for.  Every thread's place in the tile is fixed across tiles.
+// The tile's row / column block and its base element advance by masked
+// additions instead of a division and two bit deposits per tile: with every
+// bit outside mask M set, pdep(x, M) + pdep(d, M) carries across the gaps,
+// so ((P | ~M) + pdep(d, M)) & M = pdep(x + d, M) (modulo the mask's width:
+// the column block wraps and carries into the row block).  LEAN (for a
+// caller with a tight register budget, which runs this loop as a call and
+// saves its live registers once per call): the tile base is deposited per
+// tile and the output mode dispatched per store, which keep fewer values
+// live.
+template <int KB, int QM, bool RM, bool LEAN>
+__device__ __forceinline__ void smallk_tiles_body(const StepArgs &sa, const EpiTables *tb, int pitch, int gmode,
+                                                  int64_t col_tiles, int64_t t0, int64_t t_end, int64_t stride,
+                                                  float *buf, int gt, int bid) {
     constexpr int K = 1 << KB;
     constexpr int QN = 3 - QM;
+    if (t0 >= t_end) return;
+    __builtin_assume(__isShared(buf));
+    __builtin_assume(__isShared(tb));
     const EpiParams &e = sa.epi;
     const int a = e.a_bits, b = e.b_bits;
     const int Me = 1 << a, Ne = 1 << b;
     const int PA = Me + 4, PB = Ne + 4;
     float *As = buf, *Bs = buf + K * PA;
-    const float *A = (const float *)sa.A + (rt << a) * (int64_t)K;
-    const float *B = (const float *)sa.B + (ct << b) * (int64_t)K;
-    // operands: rows [rt 2^a, (rt + 1) 2^a) of A and the tile's columns of B,
-    // contiguous in memory; transposed to [k][row] / [k][col]
-    if constexpr (K == 1) {
-        for (int f = gt; f < Me / 4; f += 128) *(float4 *)&As[4 * f] = *(const float4 *)(A + 4 * f);
-        for (int f = gt; f < Ne / 4; f += 128) *(float4 *)&Bs[4 * f] = *(const float4 *)(B + 4 * f);
-    } else {
-        constexpr int KQ = K / 4, LKQ = KB - 2;
-        for (int f = gt; f < Me * KQ; f += 128) {
-            const float4 v = *(const float4 *)(A + 4 * (int64_t)f);
-            const int r = f >> LKQ, k = (f & (KQ - 1)) * 4;
-            As[k * PA + r] = v.x;
-            As[(k + 1) * PA + r] = v.y;
-            As[(k + 2) * PA + r] = v.z;
-            As[(k + 3) * PA + r] = v.w;
-        }
-        for (int f = gt; f < Ne * KQ; f += 128) {
-            const float4 v = *(const float4 *)(B + 4 * (int64_t)f);
-            const int c = f >> LKQ, k = (f & (KQ - 1)) * 4;
-            Bs[k * PB + c] = v.x;
-            Bs[(k + 1) * PB + c] = v.y;
-            Bs[(k + 2) * PB + c] = v.z;
-            Bs[(k + 3) * PB + c] = v.w;
-        }
-    }
-    sk_bar(bid);
     // thread (tx, ty) owns row quads ty + Y u and column quads tx + X v; the
     // lanes of a warp run along the staging buffer's contiguous dimension
     // (columns when it is row-major), so that its float4 writes are
     // conflict-free
-    const int X = (Ne >> 2) / QN, Y = (Me >> 2) / QM;
-    const int tx = rowmajor ? gt % X : gt / Y, ty = rowmajor ? gt / X : gt % Y;
-    const bool active = gt < X * Y;
-    float acc[4 * QM][4 * QN];
+    const int lX = b - 2 - (QN - 1), lY = a - 2 - (QM - 1);  // X = 2^lX, Y = 2^lY
+    const int tx = RM ? gt & ((1 << lX) - 1) : gt >> lY;
+    const int ty = RM ? gt >> lX : gt & ((1 << lY) - 1);
+    const bool active = gt < (1 << (lX + lY));
+    int oa[QM], ob[QN];
 #pragma unroll
-    for (int u = 0; u < 4 * QM; ++u)
+    for (int u = 0; u < QM; ++u) oa[u] = 4 * (ty + (u << lY));
 #pragma unroll
-        for (int v = 0; v < 4 * QN; ++v) acc[u][v] = 0.f;
-    if (active) {
-#pragma unroll
-        for (int k = 0; k < K; ++k) {
-            float4 av[QM], bv[QN];
-#pragma unroll
-            for (int u = 0; u < QM; ++u) av[u] = *(const float4 *)&As[k * PA + 4 * (ty + Y * u)];
-#pragma unroll
-            for (int v = 0; v < QN; ++v) bv[v] = *(const float4 *)&Bs[k * PB + 4 * (tx + X * v)];
-#pragma unroll
-            for (int u = 0; u < QM; ++u) {
-                const float ar[4] = {av[u].x, av[u].y, av[u].z, av[u].w};
-#pragma unroll
-                for (int v = 0; v < QN; ++v) {
-                    const float br[4] = {bv[v].x, bv[v].y, bv[v].z, bv[v].w};
-#pragma unroll
-                    for (int i = 0; i < 4; ++i)
-#pragma unroll
-                        for (int j = 0; j < 4; ++j) acc[4 * u + i][4 * v + j] = fmaf(ar[i], br[j], acc[4 * u + i][4 * v + j]);
-                }
-            }
-        }
-    }
-    sk_bar(bid);  // operands read: the staging buffer aliases them
-    float *stg = buf;
-    if (active) {
-#pragma unroll
-        for (int u = 0; u < QM; ++u)
-#pragma unroll
-            for (int v = 0; v < QN; ++v) {
-                const int r0 = 4 * (ty + Y * u), c0 = 4 * (tx + X * v);
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    if (rowmajor)
-                        *(float4 *)&stg[(r0 + i) * pitch + c0] =
-                            make_float4(acc[4 * u + i][4 * v], acc[4 * u + i][4 * v + 1], acc[4 * u + i][4 * v + 2],
-                                        acc[4 * u + i][4 * v + 3]);
-                    else
-                        *(float4 *)&stg[(c0 + i) * pitch + r0] =
-                            make_float4(acc[4 * u][4 * v + i], acc[4 * u + 1][4 * v + i], acc[4 * u + 2][4 * v + i],
-                                        acc[4 * u + 3][4 * v + i]);
-                }
-            }
-    }
-    sk_bar(bid);
-    if constexpr (LEAN) epi_readout_rt(tb, stg, e, base, Me * Ne, gt, 128, gmode);
-    else epi_readout(tb, stg, e, base, Me * Ne, gt, 128, gmode);
-    sk_bar(bid);  // the next tile's operands overwrite the staging buffer
-}
-
-// Tiles t0, t0 + stride, ... < t_end of a small-K step (col_tiles: a power
-// of two).  The tile's row / column block and its base element advance by
-// masked additions instead of a division and two bit deposits per tile:
-// with every bit outside mask M set, pdep(x, M) + pdep(d, M) carries across
-// the gaps, so ((P | ~M) + pdep(d, M)) & M = pdep(x + d, M) (modulo the
-// mask's width: the column block wraps and carries into the row block).
-// LEAN (for a caller with a tight register budget, which saves its live
-// registers once per call of this non-inlined loop): the tile base is
-// deposited per tile and the output mode dispatched per store, which keep
-// fewer values live.
-template <int KB, int QM, bool LEAN>
-__device__ __noinline__ void smallk_tiles(const StepArgs &sa, const EpiTables *tb, int rowmajor, int pitch, int gmode,
-                                          int64_t col_tiles, int64_t t0, int64_t t_end, int64_t stride, float *buf,
-                                          int gt, int bid) {
-    if (t0 >= t_end) return;
-    const EpiParams &e = sa.epi;
+    for (int v = 0; v < QN; ++v) ob[v] = 4 * (tx + (v << lX));
     const int lct = __ffsll((long long)col_tiles) - 1;
     const int64_t cmask = col_tiles - 1;
-    if constexpr (LEAN) {
-        for (int64_t t = t0; t < t_end; t += stride) {
-            const int64_t r = t >> lct, c = t & cmask;
-            smallk_tile_run<KB, QM, true>(sa, tb, rowmajor, pitch, gmode, r, c, tile_base(e, r, c), buf, gt, bid);
-        }
-        return;
-    }
     const int64_t sc = stride & cmask, sr = stride >> lct;
     int64_t rt = t0 >> lct, ct = t0 & cmask;
-    uint64_t pr = pdep64((uint64_t)rt, e.highR), pc = pdep64((uint64_t)ct, e.highC);
-    const uint64_t dc = pdep64((uint64_t)sc, e.highC);
-    const uint64_t dr0 = pdep64((uint64_t)sr, e.highR), dr1 = pdep64((uint64_t)sr + 1, e.highR);
+    uint64_t pr = 0, pc = 0, dc = 0, dr0 = 0, dr1 = 0;
+    if constexpr (!LEAN) {
+        pr = pdep64((uint64_t)rt, e.highR);
+        pc = pdep64((uint64_t)ct, e.highC);
+        dc = pdep64((uint64_t)sc, e.highC);
+        dr0 = pdep64((uint64_t)sr, e.highR);
+        dr1 = pdep64((uint64_t)sr + 1, e.highR);
+    }
     for (int64_t t = t0; t < t_end; t += stride) {
-        smallk_tile_run<KB, QM, false>(sa, tb, rowmajor, pitch, gmode, rt, ct, pr | pc, buf, gt, bid);
-        const int64_t c2 = ct + sc;
-        const int carry = (int)(c2 >> lct);
-        ct = c2 & cmask;
-        rt += sr + carry;
-        pc = ((pc | ~e.highC) + dc) & e.highC;
-        pr = ((pr | ~e.highR) + (carry ? dr1 : dr0)) & e.highR;
+        if constexpr (LEAN) {
+            rt = t >> lct;
+            ct = t & cmask;
+        }
+        const float *A = (const float *)sa.A + (rt << a) * (int64_t)K;
+        const float *B = (const float *)sa.B + (ct << b) * (int64_t)K;
+        // operands: rows [rt 2^a, (rt + 1) 2^a) of A and the tile's columns of
+        // B, contiguous in memory; transposed to [k][row] / [k][col]
+        if constexpr (K == 1) {
+            for (int f = gt; f < Me / 4; f += 128) *(float4 *)&As[4 * f] = *(const float4 *)(A + 4 * f);
+            for (int f = gt; f < Ne / 4; f += 128) *(float4 *)&Bs[4 * f] = *(const float4 *)(B + 4 * f);
+        } else {
+            constexpr int KQ = K / 4, LKQ = KB - 2;
+            for (int f = gt; f < Me * KQ; f += 128) {
+                const float4 v = *(const float4 *)(A + 4 * (int64_t)f);
+                float *d = As + (f & (KQ - 1)) * 4 * PA + (f >> LKQ);
+                d[0] = v.x;
+                d[PA] = v.y;
+                d[2 * PA] = v.z;
+                d[3 * PA] = v.w;
+            }
+            for (int f = gt; f < Ne * KQ; f += 128) {
+                const float4 v = *(const float4 *)(B + 4 * (int64_t)f);
+                float *d = Bs + (f & (KQ - 1)) * 4 * PB + (f >> LKQ);
+                d[0] = v.x;
+                d[PB] = v.y;
+                d[2 * PB] = v.z;
+                d[3 * PB] = v.w;
+            }
+        }
+        sk_bar(bid);
+        float acc[4 * QM][4 * QN];
+#pragma unroll
+        for (int u = 0; u < 4 * QM; ++u)
+#pragma unroll
+            for (int v = 0; v < 4 * QN; ++v) acc[u][v] = 0.f;
+        if (active) {
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                float4 av[QM], bv[QN];
+#pragma unroll
+                for (int u = 0; u < QM; ++u) av[u] = *(const float4 *)&As[k * PA + oa[u]];
+#pragma unroll
+                for (int v = 0; v < QN; ++v) bv[v] = *(const float4 *)&Bs[k * PB + ob[v]];
+#pragma unroll
+                for (int u = 0; u < QM; ++u) {
+                    const float ar[4] = {av[u].x, av[u].y, av[u].z, av[u].w};
+#pragma unroll
+                    for (int v = 0; v < QN; ++v) {
+                        const float br[4] = {bv[v].x, bv[v].y, bv[v].z, bv[v].w};
+#pragma unroll
+                        for (int i = 0; i < 4; ++i)
+#pragma unroll
+                            for (int j = 0; j < 4; ++j)
+                                acc[4 * u + i][4 * v + j] = fmaf(ar[i], br[j], acc[4 * u + i][4 * v + j]);
+                    }
+                }
+            }
+        }
+        sk_bar(bid);  // operands read: the staging buffer aliases them
+        float *stg = buf;
+        if (active) {
+#pragma unroll
+            for (int u = 0; u < QM; ++u)
+#pragma unroll
+                for (int v = 0; v < QN; ++v) {
+                    float *d = RM ? stg + oa[u] * pitch + ob[v] : stg + ob[v] * pitch + oa[u];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        if constexpr (RM)
+                            *(float4 *)(d + i * pitch) = make_float4(acc[4 * u + i][4 * v], acc[4 * u + i][4 * v + 1],
+                                                                     acc[4 * u + i][4 * v + 2], acc[4 * u + i][4 * v + 3]);
+                        else
+                            *(float4 *)(d + i * pitch) = make_float4(acc[4 * u][4 * v + i], acc[4 * u + 1][4 * v + i],
+                                                                     acc[4 * u + 2][4 * v + i], acc[4 * u + 3][4 * v + i]);
+                    }
+                }
+        }
+        sk_bar(bid);
+        if constexpr (LEAN) {
+            epi_readout_rt(tb, stg, e, tile_base(e, (uint64_t)rt, (uint64_t)ct), Me * Ne, gt, 128, gmode);
+        } else {
+            epi_readout(tb, stg, e, pr | pc, Me * Ne, gt, 128, gmode);
+            const int64_t c2 = ct + sc;
+            const int carry = (int)(c2 >> lct);
+            ct = c2 & cmask;
+            rt += sr + carry;
+            pc = ((pc | ~e.highC) + dc) & e.highC;
+            pr = ((pr | ~e.highR) + (carry ? dr1 : dr0)) & e.highR;
+        }
+        sk_bar(bid);  // the next tile's operands overwrite the staging buffer
     }
 }
 
+template <int KB, int QM, bool RM>
+__device__ __noinline__ void smallk_tiles_lean(const StepArgs &sa, const EpiTables *tb, int pitch, int gmode,
+                                               int64_t col_tiles, int64_t t0, int64_t t_end, int64_t stride,
+                                               float *buf, int gt, int bid) {
+    smallk_tiles_body<KB, QM, RM, true>(sa, tb, pitch, gmode, col_tiles, t0, t_end, stride, buf, gt, bid);
+}
+
+template <int KB, int QM, bool RM, bool LEAN>
+__device__ __forceinline__ void smallk_tiles(const StepArgs &sa, const EpiTables *tb, int pitch, int gmode,
+                                             int64_t col_tiles, int64_t t0, int64_t t_end, int64_t stride, float *buf,
+                                             int gt, int bid) {
+    if constexpr (LEAN) smallk_tiles_lean<KB, QM, RM>(sa, tb, pitch, gmode, col_tiles, t0, t_end, stride, buf, gt, bid);
+    else smallk_tiles_body<KB, QM, RM, false>(sa, tb, pitch, gmode, col_tiles, t0, t_end, stride, buf, gt, bid);
+}
+
+// The instance for the step's K, tile width and staging orientation.
 template <bool LEAN>
 __device__ __forceinline__ void smallk_dispatch(const StepArgs &sa, const EpiTables *tb, int rowmajor, int pitch,
                                                 int gmode, int64_t col_tiles, int64_t t0, int64_t t_end,
                                                 int64_t stride, float *buf, int gt, int bid) {
     const bool wide = sa.epi.b_bits >= 3;
-#define TQC_SMALLK_CASE(KBV)                                                                                      \
-    if (sa.kb == KBV) {                                                                                           \
-        if (wide)                                                                                                 \
-            smallk_tiles<KBV, 1, LEAN>(sa, tb, rowmajor, pitch, gmode, col_tiles, t0, t_end, stride, buf, gt, bid); \
-        else                                                                                                      \
-            smallk_tiles<KBV, 2, LEAN>(sa, tb, rowmajor, pitch, gmode, col_tiles, t0, t_end, stride, buf, gt, bid); \
-        return;                                                                                                   \
+#define TQC_SMALLK_CASE(KBV, QMV, RMV)                                                                         \
+    if (sa.kb == KBV && (QMV == 1) == wide && (rowmajor != 0) == RMV) {                                        \
+        smallk_tiles<KBV, QMV, RMV, LEAN>(sa, tb, pitch, gmode, col_tiles, t0, t_end, stride, buf, gt, bid); \
+        return;                                                                                                \
     }
-    TQC_SMALLK_CASE(0)
-    TQC_SMALLK_CASE(2)
-    TQC_SMALLK_CASE(4)
+    TQC_SMALLK_CASE(0, 1, true)
+    TQC_SMALLK_CASE(0, 1, false)
+    TQC_SMALLK_CASE(0, 2, true)
+    TQC_SMALLK_CASE(0, 2, false)
+    TQC_SMALLK_CASE(2, 1, true)
+    TQC_SMALLK_CASE(2, 1, false)
+    TQC_SMALLK_CASE(2, 2, true)
+    TQC_SMALLK_CASE(2, 2, false)
+    TQC_SMALLK_CASE(4, 1, true)
+    TQC_SMALLK_CASE(4, 1, false)
+    TQC_SMALLK_CASE(4, 2, true)
+    TQC_SMALLK_CASE(4, 2, false)
 #undef TQC_SMALLK_CASE
 }
 
