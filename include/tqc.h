@@ -275,7 +275,10 @@ TQC_API tqc_status tqc_contract_host(tqc_plan_t plan, const void *const *host_te
  * Many plans (independent networks of uneven sizes) in one persistent launch:
  * one kernel drains a device work list of every plan's ingest chunks and
  * step tiles (CUDA-core and tcgen05), each waiting, with a bounded wait, on
- * the counters of the items that produce its operands.  d_outs[i] receives
+ * the counters of the items that produce its operands.  A plan's steps from
+ * its first large one on (predicted to take at least the threshold of
+ * tqc_batch_tail_threshold) run after that kernel, on the same stream, as
+ * the ordinary step kernels of tqc_contract.  d_outs[i] receives
  * plan i's bin (FP32, renormalised with the plan's cached total mass).
  * Requirements: every plan was contracted once since its tensors last
  * changed, and none is sliced (TQC_ERR_UNSUPPORTED otherwise).  The first
@@ -288,8 +291,21 @@ TQC_API tqc_status tqc_contract_batch(const tqc_plan_t *plans, void *const *d_ou
                                       void *cuda_stream);
 
 /* Synchronise `cuda_stream` and report the last batched launch:
- * TQC_ERR_TIMEOUT if one of its bounded device waits gave up. */
+ * TQC_ERR_TIMEOUT if one of its bounded device waits gave up (in the
+ * persistent kernel, or in a large step launched after it). */
 TQC_API tqc_status tqc_batch_status(void *cuda_stream);
+
+/* Predicted step time (seconds, cost model of tqc_plan) from which a plan's
+ * steps leave the persistent kernel of tqc_contract_batch and run as their
+ * own launches after it: 0 = every step, a huge value = none; default 16e-6.
+ * TQC_ERR_INVALID for a negative or NaN value. */
+TQC_API tqc_status tqc_batch_tail_threshold(double seconds);
+
+/* Kernel launches of one tqc_contract_batch call with the last list (the
+ * persistent kernel plus the large steps' own launches) and the number of
+ * steps that ran after it (tail_steps may be NULL).  TQC_ERR_INVALID before
+ * any batch was launched. */
+TQC_API tqc_status tqc_batch_launches(int64_t *launches, int64_t *tail_steps);
 
 /* Fault-injection hook for tests: while enabled, batched launches carry one
  * extra item that waits on a counter nothing increments, so its bounded wait

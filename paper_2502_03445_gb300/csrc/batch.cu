@@ -51,7 +51,7 @@ struct alignas(128) BStep {
     int32_t klass, prec, bn, k_blocks, bres;
     int32_t gmode;        // CUDA-core tiles: gather mode of the staged write-out
     int32_t smallk;       // CUDA-core tiles of the small-K form (smallk.cuh), with
-    int32_t sk_rowmajor, sk_pitch;  // its staging orientation and pitch
+    SmallkLayout sk;      // its write-out layout
     int64_t col_tiles;
     int32_t dep[2];
     int64_t need[2];
@@ -409,8 +409,8 @@ __global__ void __launch_bounds__(BT, 1)
                 bar_sync(2 + g, 128);
                 const BStep &st = steps[item.idx];
                 if (st.smallk)
-                    smallk_dispatch<true>(st.a, tb, st.sk_rowmajor, st.sk_pitch, st.gmode, st.col_tiles, item.tile + g,
-                                    item.tile + item.count, 4, (float *)buf, gt, 2 + g);
+                    smallk_dispatch<true>(st.a, tb, st.sk, st.col_tiles, item.tile + g, item.tile + item.count, 4,
+                                          (float *)buf, gt, 2 + g);
                 else
                     simt_range(st, tb, item.tile + g, item.tile + item.count, buf, 2 + g, gt);
             }
@@ -634,8 +634,20 @@ void host_tables(EpiTables *tb, const EpiParams &e, bool rowmajor, int pitch) {
     }
 }
 
+// A plan's steps from its first large one on (predicted by the cost model
+// to take at least g_tail_s) run after the persistent kernel as ordinary
+// step launches: a large step fills the GPU by itself and runs faster in its
+// own kernels (all warps of every SM, its own register budget) than as
+// items of the persistent kernel, while the small ones gain from sharing it.
+struct BatchTail {
+    Plan *p;
+    size_t first;
+    void *out;
+};
+
 struct Batch {
     std::vector<const void *> key;
+    std::vector<BatchTail> tails;
     BItem *d_items = nullptr;
     BStep *d_steps = nullptr;
     EpiTables *d_tables = nullptr;
@@ -657,6 +669,7 @@ struct Batch {
 std::mutex g_batch_mu;
 Batch g_batch;
 int g_inject_stall = 0;
+double g_tail_s = 16e-6;
 
 template <typename T>
 cudaError_t upload(T **dst, const std::vector<T> &v) {
@@ -716,7 +729,19 @@ tqc_status build_batch(Plan *const *plans, void *const *outs, int n, Batch *b) {
             counter_of[j] = ing_counter;
             tiles_of[j] = n_chunks;
         }
-        for (const StepPlan &sp : p.steps) {
+        size_t first_tail = p.steps.size();
+        const CostConsts cc;
+        for (size_t i = 0; i < p.steps.size(); ++i) {
+            const StepPlan &sp = p.steps[i];
+            if (step_cost(sp.mb, sp.nb, sp.kb, sp.klass, sp.prec, cc).time_s - cc.launch_s >= g_tail_s) {
+                first_tail = i;
+                break;
+            }
+        }
+        if (first_tail < p.steps.size() && first_tail > 0 && p.steps[first_tail].fuse == 2) --first_tail;
+        if (first_tail < p.steps.size()) b->tails.push_back(BatchTail{&p, first_tail, outs[pi]});
+        for (size_t si0 = 0; si0 < first_tail; ++si0) {
+            const StepPlan &sp = p.steps[si0];
             BStep bs;
             std::memset((void *)&bs, 0, sizeof bs);
             bs.klass = sp.klass;
@@ -754,11 +779,8 @@ tqc_status build_batch(Plan *const *plans, void *const *outs, int n, Batch *b) {
                 bs.col_tiles = (int64_t)1 << (sp.nb - bs.a.epi.b_bits);
                 bs.gmode = gather_mode(bs.a.epi.lowCc);
                 if (smallk) {
-                    const StagePick pk = pick_staging(bs.a.epi.lowRc, bs.a.epi.lowCc);
                     bs.smallk = 1;
-                    bs.sk_rowmajor = pk.rowmajor;
-                    bs.sk_pitch = pk.rowmajor ? (1 << bs.a.epi.b_bits) + 4 : (1 << bs.a.epi.a_bits) + 4;
-                    bs.gmode = pk.gmode;
+                    bs.sk = smallk_layout(bs.a.epi);
                 }
             }
             const int64_t n_tiles = row_tiles * bs.col_tiles;
@@ -778,7 +800,7 @@ tqc_status build_batch(Plan *const *plans, void *const *outs, int n, Batch *b) {
             level_of[sp.c] = lvl;
             EpiTables tb;
             // staged write-out of the CUDA-core tiles (64 x 64 row-major, or the small-K form's)
-            if (bs.smallk) host_tables(&tb, bs.a.epi, bs.sk_rowmajor != 0, bs.sk_pitch);
+            if (bs.smallk) host_tables(&tb, bs.a.epi, bs.sk.rowmajor != 0, bs.sk.pitch);
             else host_tables(&tb, bs.a.epi, true, 68);
             const int si = (int)steps.size();
             steps.push_back(bs);
@@ -828,6 +850,7 @@ tqc_status tqc_contract_batch(const tqc_plan_t *plans, void *const *d_outs, int3
         key.push_back(d_outs[i]);
     }
     key.push_back((const void *)(intptr_t)g_inject_stall);
+    key.push_back((const void *)(intptr_t)(int64_t)(std::min(g_tail_s, 1e6) * 1e9));
     if (key != g_batch.key) {
         g_batch.release();
         std::vector<Plan *> ps;
@@ -852,6 +875,10 @@ tqc_status tqc_contract_batch(const tqc_plan_t *plans, void *const *d_outs, int3
                                         g_batch.d_err);
     e = cudaGetLastError();
     if (e != cudaSuccess) return fail(TQC_ERR_CUDA, std::string("batch launch: ") + cudaGetErrorString(e));
+    for (const BatchTail &t : g_batch.tails) {
+        tqc_status st = exec_run_tail(*t.p, t.first, t.out, cuda_stream);
+        if (st != TQC_OK) return st;
+    }
     return TQC_OK;
 }
 
@@ -863,6 +890,41 @@ tqc_status tqc_batch_status(void *cuda_stream) {
     if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)cuda_stream);
     if (e != cudaSuccess) return fail(TQC_ERR_CUDA, std::string("batch status: ") + cudaGetErrorString(e));
     if (h) return fail(TQC_ERR_TIMEOUT, "a bounded wait in the batched launch gave up");
+    // the large steps' error words (their plans' own; cleared when read)
+    for (const BatchTail &t : g_batch.tails) {
+        int w = 0;
+        e = cudaMemcpyAsync(&w, t.p->d_zinfo + 2, sizeof(int), cudaMemcpyDeviceToHost, (cudaStream_t)cuda_stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)cuda_stream);
+        if (e != cudaSuccess) return fail(TQC_ERR_CUDA, std::string("batch status: ") + cudaGetErrorString(e));
+        if (w) {
+            cudaMemsetAsync(t.p->d_zinfo + 2, 0, sizeof(int), (cudaStream_t)cuda_stream);
+            return fail(TQC_ERR_TIMEOUT, "a tensor-core step of the batch gave up waiting on its pipeline");
+        }
+    }
+    return TQC_OK;
+}
+
+tqc_status tqc_batch_launches(int64_t *launches, int64_t *tail_steps) {
+    if (!launches) return fail(TQC_ERR_INVALID, "NULL launches");
+    std::lock_guard<std::mutex> lk(g_batch_mu);
+    if (!g_batch.d_err) return fail(TQC_ERR_INVALID, "no batch launched");
+    int64_t n = 1, steps = 0;  // the persistent kernel, then each large step's launches
+    for (const BatchTail &t : g_batch.tails)
+        for (size_t i = t.first; i < t.p->steps.size(); ++i) {
+            const StepPlan &sp = t.p->steps[i];
+            ++steps;
+            if (sp.fuse == 2) continue;
+            n += sp.ksplit > 1 ? 2 : 1;
+        }
+    *launches = n;
+    if (tail_steps) *tail_steps = steps;
+    return TQC_OK;
+}
+
+tqc_status tqc_batch_tail_threshold(double seconds) {
+    if (!(seconds >= 0.0)) return fail(TQC_ERR_INVALID, "threshold must be >= 0");
+    std::lock_guard<std::mutex> lk(g_batch_mu);
+    g_tail_s = seconds;
     return TQC_OK;
 }
 

@@ -678,4 +678,19 @@ tqc_status exec_contract(Plan *p, const uint8_t *fixed_bits, void *d_out, int ou
     return TQC_OK;
 }
 
+// The steps first..end of a plan whose leaf operands and earlier results
+// are already in its workspace (the batched launch's large steps), launched
+// as tqc_contract would launch them, with the plan's cached total mass.
+tqc_status exec_run_tail(Plan &p, size_t first, void *d_out, void *stream) {
+    ExecCtx c;
+    c.ws = p.d_ws;
+    c.zws = p.d_zws;
+    c.zinfo = p.d_zinfo;
+    c.kpart = p.d_kpart;
+    std::vector<char> keep(p.tensors.size(), 0);
+    for (int j = 0; j < p.m; ++j) keep[(size_t)j] = 1;
+    for (size_t i = 0; i < first && i < p.steps.size(); ++i) keep[(size_t)p.steps[i].c] = 1;
+    return exec_run(p, c, nullptr, d_out, TQC_F32, stream, nullptr, &keep);
+}
+
 }  // namespace tqc

@@ -93,16 +93,21 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
 }
 
 
-// Small-K step (smallk.cuh): one 128-thread CTA per tile slot, the staging
-// tables built once per CTA.
-__global__ void __launch_bounds__(128, 8) simt_smallk_f32(StepArgs args, int64_t n_tiles, int64_t col_tiles, int rowmajor,
-                                                       int pitch, int gmode) {
+// Small-K step (smallk.cuh): one 128-thread CTA per tile slot, one kernel
+// per K, tile width and orientation (each with its own register budget);
+// when the tiles are staged, the staging tables are built once per CTA.
+template <int KB, int QM, bool RM>
+__global__ void __launch_bounds__(128, (QM == 1) == RM ? 8 : 6)
+    simt_smallk_f32(StepArgs args, int64_t n_tiles, int64_t col_tiles, SmallkLayout L) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     EpiTables *tb = (EpiTables *)smem_raw;
     float *buf = (float *)(smem_raw + sizeof(EpiTables));
-    epi_tables_init(tb, args.epi, rowmajor != 0, pitch, threadIdx.x, 128);
-    __syncthreads();
-    smallk_dispatch<false>(args, tb, rowmajor, pitch, gmode, col_tiles, blockIdx.x, n_tiles, gridDim.x, buf, threadIdx.x, 1);
+    if (!L.direct) {
+        epi_tables_init(tb, args.epi, RM, L.pitch, threadIdx.x, 128);
+        __syncthreads();
+    }
+    smallk_tiles_body<KB, QM, RM, false>(args, tb, L.direct, L.pitch, L.gmode, col_tiles, blockIdx.x, n_tiles,
+                                         gridDim.x, buf, threadIdx.x, 1);
 }
 
 // FP64 twin for the scalar total-mass network (small; one config).
@@ -318,28 +323,92 @@ TileShape smallk_tile(int mb, int nb, int kb) {
     return TileShape{a, b};
 }
 
+static uint64_t host_pdep64(uint64_t src, uint64_t mask) {
+    uint64_t r = 0;
+    while (mask) {
+        const uint64_t low = mask & (~mask + 1);
+        if (src & 1) r |= low;
+        src >>= 1;
+        mask ^= low;
+    }
+    return r;
+}
+
+// Direct stores when the result's lowest four or more bits are bits of one
+// tile dimension and at least two lanes run along it (whole 32-byte sectors
+// per warp store), else staging in the orientation pick_staging chooses.
+SmallkLayout smallk_layout(const EpiParams &e) {
+    SmallkLayout L;
+    const uint64_t mR = host_pdep64(e.lowRc, e.tileMask), mC = host_pdep64(e.lowCc, e.tileMask);
+    auto run = [](uint64_t m) {
+        int r = 0;
+        while (r < 64 && (m >> r & 1)) ++r;
+        return r;
+    };
+    // two quads along the lanes' dimension when the tile allows (8 of them)
+    const int a = e.a_bits, b = e.b_bits;
+    auto qm_for = [&](int rm) { return ((!rm && a >= 3) || b < 3) ? 2 : 1; };
+    auto lanes = [&](int rm) {  // log2 of the lanes along that dimension
+        const int qm = qm_for(rm);
+        return rm ? b - 2 - (2 - qm) : a - 2 - (qm - 1);
+    };
+    const StagePick pk = pick_staging(e.lowRc, e.lowCc);
+    L.rowmajor = pk.rowmajor;
+    L.gmode = pk.gmode;
+    L.pitch = pk.rowmajor ? (1 << b) + 4 : (1 << a) + 4;
+    L.direct = 0;
+    if (run(mC) >= 4 && lanes(1) >= 1) {
+        L.direct = 1;
+        L.rowmajor = 1;
+    } else if (run(mR) >= 4 && lanes(0) >= 1) {
+        L.direct = 1;
+        L.rowmajor = 0;
+    }
+    L.qm = qm_for(L.rowmajor);
+    return L;
+}
+
 cudaError_t launch_smallk(const StepArgs &a, cudaStream_t s) {
     const EpiParams &e = a.epi;
     if (!smallk_ok(a.mb, a.nb, a.kb, a.kblk != 0) || e.a_bits < 2 || e.b_bits < 2 || a.ksplit != 1)
         return cudaErrorInvalidValue;
-    const StagePick pk = pick_staging(e.lowRc, e.lowCc);
-    const int pitch = pk.rowmajor ? (1 << e.b_bits) + 4 : (1 << e.a_bits) + 4;
+    const SmallkLayout L = smallk_layout(e);
     const int bytes = std::max(smallk_op_bytes(e.a_bits, e.b_bits, a.kb),
-                               smallk_stage_bytes(e.a_bits, e.b_bits, pk.rowmajor != 0));
+                               L.direct ? 0 : smallk_stage_bytes(e.a_bits, e.b_bits, L.rowmajor != 0));
     if (bytes > SMALLK_BYTES) return cudaErrorInvalidValue;
     const size_t smem = sizeof(EpiTables) + (size_t)bytes;
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t err = cudaFuncSetAttribute(simt_smallk_f32, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)(sizeof(EpiTables) + SMALLK_BYTES));
-        if (err != cudaSuccess) return err;
-        attr = true;
-    }
     const int64_t col_tiles = 1ll << (a.nb - e.b_bits);
     const int64_t n_tiles = (1ll << (a.mb - e.a_bits)) * col_tiles;
-    const int64_t grid = std::min<int64_t>(n_tiles, (int64_t)sm_count() * 16);
-    simt_smallk_f32<<<(unsigned)grid, 128, smem, s>>>(a, n_tiles, col_tiles, pk.rowmajor, pitch, pk.gmode);
-    return cudaGetLastError();
+    const unsigned grid = (unsigned)std::min<int64_t>(n_tiles, (int64_t)sm_count() * 16);
+    const bool rm = L.rowmajor != 0;
+    static bool attr[3][2][2] = {};
+#define TQC_SMALLK_LAUNCH(KBV, QMV, RMV)                                                                      \
+    if (a.kb == KBV && L.qm == QMV && rm == RMV) {                                                           \
+        bool &done = attr[KBV / 2][QMV - 1][RMV ? 1 : 0];                                                    \
+        if (!done) {                                                                                         \
+            cudaError_t err = cudaFuncSetAttribute(simt_smallk_f32<KBV, QMV, RMV>,                           \
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize,             \
+                                                   (int)(sizeof(EpiTables) + SMALLK_BYTES));                 \
+            if (err != cudaSuccess) return err;                                                              \
+            done = true;                                                                                     \
+        }                                                                                                    \
+        simt_smallk_f32<KBV, QMV, RMV><<<grid, 128, smem, s>>>(a, n_tiles, col_tiles, L);                    \
+        return cudaGetLastError();                                                                           \
+    }
+    TQC_SMALLK_LAUNCH(0, 1, true)
+    TQC_SMALLK_LAUNCH(0, 1, false)
+    TQC_SMALLK_LAUNCH(0, 2, true)
+    TQC_SMALLK_LAUNCH(0, 2, false)
+    TQC_SMALLK_LAUNCH(2, 1, true)
+    TQC_SMALLK_LAUNCH(2, 1, false)
+    TQC_SMALLK_LAUNCH(2, 2, true)
+    TQC_SMALLK_LAUNCH(2, 2, false)
+    TQC_SMALLK_LAUNCH(4, 1, true)
+    TQC_SMALLK_LAUNCH(4, 1, false)
+    TQC_SMALLK_LAUNCH(4, 2, true)
+    TQC_SMALLK_LAUNCH(4, 2, false)
+#undef TQC_SMALLK_LAUNCH
+    return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_simt_step(int cfg, const StepArgs &a, cudaStream_t s) {

@@ -30,12 +30,67 @@ __host__ __device__ inline int smallk_stage_bytes(int a, int b, bool rowmajor) {
     return rowmajor ? (1 << a) * ((1 << b) + 4) * 4 : (1 << b) * ((1 << a) + 4) * 4;
 }
 
+// How a small-K step writes its tiles.  direct: the result's lowest bits
+// (at least four) are bits of one dimension of the tile, so each thread's
+// float4 quads along that dimension are 16 contiguous bytes and the lanes
+// of a warp run along it: results go from registers straight to their
+// destination, with no staging.  Otherwise the tile is staged (rowmajor,
+// pitch) and gathered in destination order (gmode).  rowmajor also says
+// which dimension the lanes run along: columns when set.  qm: row quads per
+// thread (1: 4 x 8 results, 2: 8 x 4), 2 when the lanes run along rows.
+struct SmallkLayout {
+    int direct, rowmajor, pitch, gmode, qm;
+};
+
+// The layout of a step with these epilogue parameters (host; simt.cu).
+SmallkLayout smallk_layout(const EpiParams &e);
+
+// Direct stores of a thread's QM x QN quads (output mode MODE): along
+// columns (RM) the quad of row i of column quad v goes to base + gr + gc[v],
+// gr stepping through the quad's rows by masked increments of mR; along rows
+// the quad of column j of row quad u goes to base + gr[u] + gc.
+template <int MODE, int QM, int QN, bool RM>
+__device__ __forceinline__ void sk_direct_store(const EpiParams &e, const float (&acc)[4 * QM][4 * QN], uint64_t base,
+                                                const uint64_t (&gr)[QM], const uint64_t (&gc)[QN], uint64_t mR,
+                                                uint64_t mC, float sf, double sd) {
+    if constexpr (RM) {
+#pragma unroll
+        for (int u = 0; u < QM; ++u) {
+            uint64_t g = base + gr[u];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+#pragma unroll
+                for (int v = 0; v < QN; ++v) {
+                    const float w[4] = {acc[4 * u + i][4 * v], acc[4 * u + i][4 * v + 1], acc[4 * u + i][4 * v + 2],
+                                        acc[4 * u + i][4 * v + 3]};
+                    store_vals<MODE, 4>(e, g + gc[v], w, sf, sd);
+                }
+                g = (((g - base) | ~mR) + 1 & mR) + base;
+            }
+        }
+    } else {
+#pragma unroll
+        for (int v = 0; v < QN; ++v) {
+            uint64_t g = gc[v];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+#pragma unroll
+                for (int u = 0; u < QM; ++u) {
+                    const float w[4] = {acc[4 * u][4 * v + j], acc[4 * u + 1][4 * v + j], acc[4 * u + 2][4 * v + j],
+                                        acc[4 * u + 3][4 * v + j]};
+                    store_vals<MODE, 4>(e, base + gr[u] + g, w, sf, sd);
+                }
+                g = ((g | ~mC) + 1) & mC;
+            }
+        }
+    }
+}
+
 __device__ __forceinline__ void sk_bar(int id) { asm volatile("bar.sync %0, 128;" ::"r"(id) : "memory"); }
 
 // Tiles t0, t0 + stride, ... < t_end of a small-K step (col_tiles: a power
-// of two).  KB = log2 K; QM x QN float4 quads per thread (QM = 1, QN = 2 when
-// the tile has at least 8 columns, else 2 x 1); RM: the staging buffer is
-// row-major.  gt: the thread's index in the group, bid: the group's named
+// of two).  KB = log2 K; QM x QN float4 quads per thread (1 x 2 or 2 x 1);
+// RM: the lanes run along columns (a staging buffer is row-major).  gt: the thread's index in the group, bid: the group's named
 // barrier; pitch / gmode: the staging pitch and gather mode the tables `tb`
 // were built for.  Every thread's place in the tile is fixed across tiles.
 // The tile's row / column block and its base element advance by masked
@@ -48,9 +103,9 @@ __device__ __forceinline__ void sk_bar(int id) { asm volatile("bar.sync %0, 128;
 // tile and the output mode dispatched per store, which keep fewer values
 // live.
 template <int KB, int QM, bool RM, bool LEAN>
-__device__ __forceinline__ void smallk_tiles_body(const StepArgs &sa, const EpiTables *tb, int pitch, int gmode,
-                                                  int64_t col_tiles, int64_t t0, int64_t t_end, int64_t stride,
-                                                  float *buf, int gt, int bid) {
+__device__ __forceinline__ void smallk_tiles_body(const StepArgs &sa, const EpiTables *tb, int direct, int pitch,
+                                                  int gmode, int64_t col_tiles, int64_t t0, int64_t t_end,
+                                                  int64_t stride, float *buf, int gt, int bid) {
     constexpr int K = 1 << KB;
     constexpr int QN = 3 - QM;
     if (t0 >= t_end) return;
@@ -74,10 +129,22 @@ __device__ __forceinline__ void smallk_tiles_body(const StepArgs &sa, const EpiT
     for (int u = 0; u < QM; ++u) oa[u] = 4 * (ty + (u << lY));
 #pragma unroll
     for (int v = 0; v < QN; ++v) ob[v] = 4 * (tx + (v << lX));
+    // direct stores: element offsets (in the tile) of the thread's first row
+    // of each row quad and first column of each column quad; the rows and
+    // columns within a quad follow by masked increments
+    const uint64_t mR = pdep64(e.lowRc, e.tileMask), mC = pdep64(e.lowCc, e.tileMask);
+    uint64_t gr[QM], gc[QN];
+    if (direct) {
+#pragma unroll
+        for (int u = 0; u < QM; ++u) gr[u] = pdep64((uint64_t)oa[u], mR);
+#pragma unroll
+        for (int v = 0; v < QN; ++v) gc[v] = pdep64((uint64_t)ob[v], mC);
+    }
+    // tile counts fit 32 bits (2^31 tiles of 2^12 results would be 2^43 results)
     const int lct = __ffsll((long long)col_tiles) - 1;
-    const int64_t cmask = col_tiles - 1;
-    const int64_t sc = stride & cmask, sr = stride >> lct;
-    int64_t rt = t0 >> lct, ct = t0 & cmask;
+    const int cmask = (int)col_tiles - 1;
+    const int sc = (int)stride & cmask, sr = (int)(stride >> lct);
+    int rt = (int)(t0 >> lct), ct = (int)t0 & cmask;
     uint64_t pr = 0, pc = 0, dc = 0, dr0 = 0, dr1 = 0;
     if constexpr (!LEAN) {
         pr = pdep64((uint64_t)rt, e.highR);
@@ -86,13 +153,13 @@ __device__ __forceinline__ void smallk_tiles_body(const StepArgs &sa, const EpiT
         dr0 = pdep64((uint64_t)sr, e.highR);
         dr1 = pdep64((uint64_t)sr + 1, e.highR);
     }
-    for (int64_t t = t0; t < t_end; t += stride) {
+    for (int t = (int)t0; t < (int)t_end; t += (int)stride) {
         if constexpr (LEAN) {
             rt = t >> lct;
             ct = t & cmask;
         }
-        const float *A = (const float *)sa.A + (rt << a) * (int64_t)K;
-        const float *B = (const float *)sa.B + (ct << b) * (int64_t)K;
+        const float *A = (const float *)sa.A + ((int64_t)rt << a) * K;
+        const float *B = (const float *)sa.B + ((int64_t)ct << b) * K;
         // operands: rows [rt 2^a, (rt + 1) 2^a) of A and the tile's columns of
         // B, contiguous in memory; transposed to [k][row] / [k][col]
         if constexpr (K == 1) {
@@ -147,6 +214,36 @@ __device__ __forceinline__ void smallk_tiles_body(const StepArgs &sa, const EpiT
             }
         }
         sk_bar(bid);  // operands read: the staging buffer aliases them
+        const uint64_t base = LEAN ? tile_base(e, (uint64_t)rt, (uint64_t)ct) : (pr | pc);
+        if (direct) {
+            if (active) {
+                const double sd = (e.mode == EPI_OUT_F32 || e.mode == EPI_OUT_F64) ? e.zinfo[1] : 1.0;
+                const float sf = (float)sd;
+#define TQC_SK_DIRECT(M) \
+    case M: sk_direct_store<M, QM, QN, RM>(e, acc, base, gr, gc, mR, mC, sf, sd); break;
+                switch (e.mode) {
+                    TQC_SK_DIRECT(EPI_F32)
+                    TQC_SK_DIRECT(EPI_TF32)
+                    TQC_SK_DIRECT(EPI_BF16)
+                    TQC_SK_DIRECT(EPI_BF16X2)
+                    TQC_SK_DIRECT(EPI_F64_SET)
+                    TQC_SK_DIRECT(EPI_F64_ADD)
+                    TQC_SK_DIRECT(EPI_OUT_F32)
+                    TQC_SK_DIRECT(EPI_OUT_F64)
+                    default: break;
+                }
+#undef TQC_SK_DIRECT
+            }
+            if constexpr (!LEAN) {
+                const int c2 = ct + sc;
+                const int carry = c2 >> lct;
+                ct = c2 & cmask;
+                rt += sr + carry;
+                pc = ((pc | ~e.highC) + dc) & e.highC;
+                pr = ((pr | ~e.highR) + (carry ? dr1 : dr0)) & e.highR;
+            }
+            continue;
+        }
         float *stg = buf;
         if (active) {
 #pragma unroll
@@ -167,11 +264,11 @@ __device__ __forceinline__ void smallk_tiles_body(const StepArgs &sa, const EpiT
         }
         sk_bar(bid);
         if constexpr (LEAN) {
-            epi_readout_rt(tb, stg, e, tile_base(e, (uint64_t)rt, (uint64_t)ct), Me * Ne, gt, 128, gmode);
+            epi_readout_rt(tb, stg, e, base, Me * Ne, gt, 128, gmode);
         } else {
-            epi_readout(tb, stg, e, pr | pc, Me * Ne, gt, 128, gmode);
-            const int64_t c2 = ct + sc;
-            const int carry = (int)(c2 >> lct);
+            epi_readout(tb, stg, e, base, Me * Ne, gt, 128, gmode);
+            const int c2 = ct + sc;
+            const int carry = c2 >> lct;
             ct = c2 & cmask;
             rt += sr + carry;
             pc = ((pc | ~e.highC) + dc) & e.highC;
@@ -182,29 +279,31 @@ __device__ __forceinline__ void smallk_tiles_body(const StepArgs &sa, const EpiT
 }
 
 template <int KB, int QM, bool RM>
-__device__ __noinline__ void smallk_tiles_lean(const StepArgs &sa, const EpiTables *tb, int pitch, int gmode,
-                                               int64_t col_tiles, int64_t t0, int64_t t_end, int64_t stride,
-                                               float *buf, int gt, int bid) {
-    smallk_tiles_body<KB, QM, RM, true>(sa, tb, pitch, gmode, col_tiles, t0, t_end, stride, buf, gt, bid);
+__device__ __noinline__ void smallk_tiles_lean(const StepArgs &sa, const EpiTables *tb, int direct, int pitch,
+                                               int gmode, int64_t col_tiles, int64_t t0, int64_t t_end,
+                                               int64_t stride, float *buf, int gt, int bid) {
+    smallk_tiles_body<KB, QM, RM, true>(sa, tb, direct, pitch, gmode, col_tiles, t0, t_end, stride, buf, gt, bid);
 }
 
 template <int KB, int QM, bool RM, bool LEAN>
-__device__ __forceinline__ void smallk_tiles(const StepArgs &sa, const EpiTables *tb, int pitch, int gmode,
+__device__ __forceinline__ void smallk_tiles(const StepArgs &sa, const EpiTables *tb, const SmallkLayout &L,
                                              int64_t col_tiles, int64_t t0, int64_t t_end, int64_t stride, float *buf,
                                              int gt, int bid) {
-    if constexpr (LEAN) smallk_tiles_lean<KB, QM, RM>(sa, tb, pitch, gmode, col_tiles, t0, t_end, stride, buf, gt, bid);
-    else smallk_tiles_body<KB, QM, RM, false>(sa, tb, pitch, gmode, col_tiles, t0, t_end, stride, buf, gt, bid);
+    if constexpr (LEAN)
+        smallk_tiles_lean<KB, QM, RM>(sa, tb, L.direct, L.pitch, L.gmode, col_tiles, t0, t_end, stride, buf, gt, bid);
+    else
+        smallk_tiles_body<KB, QM, RM, false>(sa, tb, L.direct, L.pitch, L.gmode, col_tiles, t0, t_end, stride, buf, gt,
+                                             bid);
 }
 
 // The instance for the step's K, tile width and staging orientation.
 template <bool LEAN>
-__device__ __forceinline__ void smallk_dispatch(const StepArgs &sa, const EpiTables *tb, int rowmajor, int pitch,
-                                                int gmode, int64_t col_tiles, int64_t t0, int64_t t_end,
-                                                int64_t stride, float *buf, int gt, int bid) {
-    const bool wide = sa.epi.b_bits >= 3;
+__device__ __forceinline__ void smallk_dispatch(const StepArgs &sa, const EpiTables *tb, const SmallkLayout &L,
+                                                int64_t col_tiles, int64_t t0, int64_t t_end, int64_t stride,
+                                                float *buf, int gt, int bid) {
 #define TQC_SMALLK_CASE(KBV, QMV, RMV)                                                                         \
-    if (sa.kb == KBV && (QMV == 1) == wide && (rowmajor != 0) == RMV) {                                        \
-        smallk_tiles<KBV, QMV, RMV, LEAN>(sa, tb, pitch, gmode, col_tiles, t0, t_end, stride, buf, gt, bid); \
+    if (sa.kb == KBV && L.qm == QMV && (L.rowmajor != 0) == RMV) {                                             \
+        smallk_tiles<KBV, QMV, RMV, LEAN>(sa, tb, L, col_tiles, t0, t_end, stride, buf, gt, bid);            \
         return;                                                                                                \
     }
     TQC_SMALLK_CASE(0, 1, true)

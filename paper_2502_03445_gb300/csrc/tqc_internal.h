@@ -206,6 +206,9 @@ tqc_status exec_prepare(Plan *p);
 // synchronisation).  *z_computed tells whether the total mass was computed.
 tqc_status exec_run(Plan &p, const ExecCtx &c, const uint8_t *fixed_bits, void *d_out, int out_dtype,
                     void *stream, bool *z_computed, const std::vector<char> *keep = nullptr);
+// Steps first..end of an unsliced plan whose leaves and earlier step results
+// are already in its workspace, FP32 output (the batched launch's tail).
+tqc_status exec_run_tail(Plan &p, size_t first, void *d_out, void *stream);
 // Arbitrary state list (states.cu): P(x) of n states on a plan with no free qubits.
 tqc_status exec_contract_states(Plan *p, const uint64_t *states, int64_t n, void *d_out, int out_dtype,
                                 double *z_out, void *stream);

@@ -37,7 +37,7 @@ EXPORTS = ["tqc_network_create", "tqc_network_upload", "tqc_destroy", "tqc_plan_
            "tqc_costmodel_params", "tqc_costmodel_set_params", "tqc_costmodel_grad", "tqc_costmodel_train",
            "tqc_costmodel_predict", "tqc_costmodel_save", "tqc_costmodel_load", "tqc_plan_features",
            "tqc_plan_candidates", "tqc_batch_status", "tqc_batch_inject_stall", "tqc_step_inject_stall", "tqc_hss_norms", "tqc_hss_select",
-           "tqc_network_select", "tqc_cut_opts_default", "tqc_find_cuts", "tqc_plan_cost_report"]
+           "tqc_batch_tail_threshold", "tqc_batch_launches", "tqc_network_select", "tqc_cut_opts_default", "tqc_find_cuts", "tqc_plan_cost_report"]
 PLAN_FEATURES = 32
 
 
@@ -111,6 +111,10 @@ def lib():
         L.tqc_plan_candidates.argtypes = [vp, ctypes.POINTER(PlanOpts), i32, vp, i32p]
         L.tqc_batch_status.argtypes = [vp]
         L.tqc_batch_inject_stall.argtypes = [i32]
+        L.tqc_batch_tail_threshold.argtypes = [ctypes.c_double]
+        L.tqc_batch_tail_threshold.restype = ctypes.c_int
+        L.tqc_batch_launches.argtypes = [ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
+        L.tqc_batch_launches.restype = ctypes.c_int
         L.tqc_step_inject_stall.argtypes = [i32]
         L.tqc_step_inject_stall.restype = ctypes.c_int
         L.tqc_hss_norms.argtypes = [vp, i32, vp, vp]
@@ -537,6 +541,21 @@ def batch_status(stream=None):
     """Synchronise and raise TqcError(ERR_TIMEOUT) if the last batched
     launch had a bounded wait give up."""
     _check(lib().tqc_batch_status(_stream_ptr(stream)))
+
+
+def batch_tail_threshold(seconds: float):
+    """Predicted step time from which a plan's steps run as their own
+    launches after the persistent kernel of contract_batch (0 = every step,
+    float("inf") = none)."""
+    _check(lib().tqc_batch_tail_threshold(min(float(seconds), 1e30)))
+
+
+def batch_launches():
+    """(kernel launches per contract_batch call, steps run after the
+    persistent kernel) for the last batch list."""
+    n, t = ctypes.c_int64(), ctypes.c_int64()
+    _check(lib().tqc_batch_launches(ctypes.byref(n), ctypes.byref(t)))
+    return n.value, t.value
 
 
 def batch_inject_stall(enable: bool):

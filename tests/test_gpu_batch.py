@@ -92,6 +92,43 @@ def test_batch_matches_oracle(mode):
         p.close()
 
 
+@pytest.mark.parametrize("tail_s", [0.0, 1e-6, 3e-6])
+def test_batch_large_steps_after_the_persistent_kernel(tail_s):
+    """Steps predicted to take at least tail_s run as ordinary step launches
+    after the persistent kernel (0: every step; the kernel only ingests),
+    also when the whole batch is replayed from a CUDA graph."""
+    nets = uneven_networks()
+    hs, plans, outs, want = prepared(nets, ["auto"] * len(nets))
+    tqc.batch_tail_threshold(tail_s)
+    try:
+        tqc.contract_batch(plans, outs)
+        tqc.batch_status()
+        check(outs, want, plans)
+        launches, tail_steps = tqc.batch_launches()
+        if tail_s == 0.0:
+            assert tail_steps == sum(len(p.describe()["steps"]) for p in plans)
+        assert launches >= 1 + (tail_steps > 0) and launches <= 1 + 2 * tail_steps
+        for o in outs:
+            o.fill_(float("nan"))
+        s = torch.cuda.Stream()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            tqc.contract_batch(plans, outs, stream=s)
+        g.replay()
+        torch.cuda.synchronize()
+        tqc.batch_status()
+        check(outs, want, plans)
+    finally:
+        tqc.batch_tail_threshold(16e-6)
+    for p in plans:
+        p.close()
+
+
+def test_batch_tail_threshold_rejects_negative():
+    with pytest.raises(tqc.TqcError):
+        tqc.batch_tail_threshold(-1.0)
+
+
 def test_batch_autotuned_tiles():
     """Plans tuned by the autotuner: the batch runs each tensor-core step at
     the tile width the autotuner chose, with the same results."""
