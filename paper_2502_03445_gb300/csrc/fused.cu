@@ -190,31 +190,36 @@ __global__ void __launch_bounds__(F_THREADS, 1)
         }
     } else if (warp == 1) {
         // ------------------------------------------------ MMA issuer
+        // The next unit's step-s MMAs are issued ahead of this unit's last
+        // k-block of step s + 1 (as soon as the convert warps have read all
+        // of D0), so the tensor pipe has that k-block's MMAs to run while the
+        // convert warps start on the next D0; issued in unit order, the pipe
+        // would idle for the first k-block's conversion of every unit.
         if (lane == 0) {
             int64_t lt = 0, itb = 0;
             bool ok = true;
             const uint32_t d0 = tmem_base;
-            for (int64_t u = blockIdx.x; ok && u < P.n_units; u += gridDim.x, ++lt) {
-                // step s: D0 = A0 B0^T
-                if (!mbar_wait(ab_full, (uint32_t)(lt & 1), abort_flag) ||
-                    !mbar_wait(d0_empty, (uint32_t)((lt & 1) ^ 1), abort_flag)) {
-                    ok = false;
-                    break;
-                }
+            // step s: D0 = A0 B0^T for the unit with sequence number n
+            auto issue_step0 = [&](int64_t n) -> bool {
+                if (!mbar_wait(ab_full, (uint32_t)(n & 1), abort_flag) ||
+                    !mbar_wait(d0_empty, (uint32_t)((n & 1) ^ 1), abort_flag))
+                    return false;
                 tc_fence_after();
-                {
-                    const uint32_t a = smem_u32(smem + OFF_A0), al = a + A0_BYTES;
-                    const uint32_t b = smem_u32(smem + OFF_B0), bl = b + B0_BYTES;
+                const uint32_t a = smem_u32(smem + OFF_A0), al = a + A0_BYTES;
+                const uint32_t b = smem_u32(smem + OFF_B0), bl = b + B0_BYTES;
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        const uint64_t da = umma_desc(a + 32 * k, 128), db = umma_desc(b + 32 * k, 128);
-                        umma<K_BF16X3>(d0, da, db, IDESC0, k != 0);
-                        umma<K_BF16X3>(d0, da, umma_desc(bl + 32 * k, 128), IDESC0, 1u);
-                        umma<K_BF16X3>(d0, umma_desc(al + 32 * k, 128), db, IDESC0, 1u);
-                    }
+                for (int k = 0; k < 4; ++k) {
+                    const uint64_t da = umma_desc(a + 32 * k, 128), db = umma_desc(b + 32 * k, 128);
+                    umma<K_BF16X3>(d0, da, db, IDESC0, k != 0);
+                    umma<K_BF16X3>(d0, da, umma_desc(bl + 32 * k, 128), IDESC0, 1u);
+                    umma<K_BF16X3>(d0, umma_desc(al + 32 * k, 128), db, IDESC0, 1u);
                 }
                 umma_commit(ab_empty);
                 umma_commit(d0_full);
+                return true;
+            };
+            if ((int64_t)blockIdx.x < P.n_units) ok = issue_step0(0);
+            for (int64_t u = blockIdx.x; ok && u < P.n_units; u += gridDim.x, ++lt) {
                 // step s + 1: D1 = sum_j C0'_j B1_j^T
                 const int acc = (int)(lt & 1);
                 const uint32_t d1 = tmem_base + 256u + (uint32_t)(acc * 128);
@@ -223,6 +228,10 @@ __global__ void __launch_bounds__(F_THREADS, 1)
                     break;
                 }
                 for (int j = 0; j < 4; ++j, ++itb) {
+                    if (j == 3 && u + gridDim.x < P.n_units && !issue_step0(lt + 1)) {
+                        ok = false;
+                        break;
+                    }
                     const int sl = (int)(itb & 1);
                     const uint32_t ph = (uint32_t)((itb >> 1) & 1);
                     if (!mbar_wait(&b1_full[sl], ph, abort_flag) || !mbar_wait(&a1_full[sl], ph, abort_flag)) {
