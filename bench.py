@@ -22,6 +22,7 @@ persistent launch replayed from a CUDA graph, against sequential calls).
   python bench.py --workload qaoa48|grid64   (tensor-bound bins, one JSON line)
   python bench.py --batch 256                 (the batched launch, one JSON line)
   python bench.py --hss | --planner-eval      (heavy state selection; learned planner)
+  python bench.py --smallk all                (small-K CUDA-core steps, both tile forms)
 
 Under torchrun each rank reconstructs its own network instance (weak
 scaling, no collective on the data path); rank 0 prints one JSON line.
@@ -80,6 +81,9 @@ def parse():
     ap.add_argument("--states", type=int, default=0,
                     help="instead: time tqc_contract_states on this many grid30 states")
     ap.add_argument("--cuts", action="store_true", help="instead: the cut finder on the 48-qubit QAOA circuit")
+    ap.add_argument("--smallk", default="",
+                    help="instead: one small-K CUDA-core final step (a gen.workloads.SMALLK_CASES name, or all), "
+                         "the small-K tile against the general tiles")
     ap.add_argument("--no-sub", action="store_true",
                     help="skip the tensor_bound and batched sub-records of the default line")
     ap.add_argument("--sub-steps", type=int, default=5, help="timed steps of each sub-record")
@@ -864,12 +868,75 @@ def time_plan(torch, plan, out, steps, warmup, profile=False):
     return s.elapsed_time(e) / steps
 
 
+def measure_smallk(args, case):
+    """One small-K final step (two subcircuits sharing one or two cut edges,
+    2^27-2^28 FP32 results): the step's CUDA-event time with the small-K tile
+    and with the general tiles (TQC_FLAG_NO_SMALLK), against the measured copy
+    bandwidth over its algorithmic bytes, and sampled states against oracle A."""
+    import torch
+    import oracle
+    from gen import workloads
+    from paper_2502_03445_gb300 import tqc
+    net = workloads.smallk_network(case)
+    h = tqc.Network(net, dtype=tqc.F32)
+    hbm = peaks()[0]
+    res = {}
+    for tag, flags in (("smallk", 0), ("general", tqc.FLAG_NO_SMALLK)):
+        p = tqc.Plan(h, precision="fp32", flags=tqc.FLAG_NO_RENORM | flags)
+        o = torch.empty(p.out_elems, dtype=torch.float32, device="cuda")
+        for _ in range(max(3, args.warmup)):
+            p.contract(o)
+        torch.cuda.synchronize()
+        p.profile(True)
+        for _ in range(args.steps):
+            p.contract(o)
+        torch.cuda.synchronize()
+        d = p.describe()
+        last = len(d["steps"]) - 1
+        st = d["steps"][last]
+        ms = p.step_time(last)[0]
+        p.profile(False)
+        m, n, k = st["log2_m"], st["log2_n"], st["log2_k"]
+        alg = 4.0 * (2 ** (m + n) + 2 ** (m + k) + 2 ** (n + k))
+        gbs = alg / (ms / 1e3) / 1e9
+        res[tag] = {"ms": ms, "GB/s": gbs, "frac": gbs / hbm, "tile": st["tile"]}
+        if tag == "smallk":
+            rng = np.random.Generator(np.random.PCG64(5))
+            idx = sorted(set(int(i) for i in rng.integers(0, 1 << net.n_qubits, size=4)))
+            want = oracle.recon_states(net, idx)
+            got = o[torch.tensor(idx, device="cuda")].double().cpu().numpy()
+            res["max_abs_err_vs_oracle"] = float(np.abs(got - want).max())
+            res["max_abs_p"] = float(np.abs(want).max())
+            res["step"] = {"log2_m": m, "log2_n": n, "log2_k": k, "mask_r": hex(st["mask_r"]),
+                           "mask_c": hex(st["mask_c"])}
+            res["algorithmic_bytes"] = alg
+        p.close()
+        del o
+    h.close()
+    res["speedup_of_smallk"] = res["general"]["ms"] / res["smallk"]["ms"]
+    return res
+
+
+def run_smallk(args):
+    import torch
+    torch.cuda.set_device(0)
+    from gen import workloads
+    cases = list(workloads.SMALLK_CASES) if args.smallk == "all" else [args.smallk]
+    out = {c: measure_smallk(args, c) for c in cases}
+    print(json.dumps({"metric": "small-K CUDA-core final step, GB/s over algorithmic bytes", "unit": "GB/s",
+                      "peak": peaks()[0], "peak_kind": f"{peaks()[3]} copy bandwidth", "steps": args.steps,
+                      "cases": out}), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     if args.batch > 0:
         return run_batch(args)
+    if args.smallk:
+        return run_smallk(args)
     if args.planner_eval:
         return run_planner_eval(args)
     if args.hss:

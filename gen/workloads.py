@@ -148,6 +148,33 @@ def batch_recipe(count: int = 256, n_lo: int = 16, n_hi: int = 28, seed0: int = 
     return nets, redraws
 
 
+# Two subcircuits of a 27-28-qubit network sharing one or two cut edges (a
+# final step with K = 4 or 16): (n_qubits, cut edges, qubits of subcircuit 0
+# as (kind, count), kind "lo" / "hi" = the lowest / highest qubits, "scr" = a
+# seeded random draw; subcircuit 1 takes the rest).
+SMALLK_CASES = {
+    "16x12k4_rows_low": (28, [(0, 1)], ("lo", 16)),
+    "16x12k4_cols_low": (28, [(0, 1)], ("hi", 16)),
+    "16x12k4_scrambled": (28, [(0, 1)], ("scr", 16)),
+    "23x4k16_cols_low": (27, [(0, 1)] * 2, ("hi", 23)),
+    "16x12k16_rows_low": (28, [(0, 1)] * 2, ("lo", 16)),
+    "16x12k16_scrambled": (28, [(0, 1)] * 2, ("scr", 16)),
+}
+
+
+def smallk_network(case: str, seed: int = 1) -> Network:
+    """The network of one SMALLK_CASES entry, pseudo-physical tensors."""
+    n, edges, (kind, cnt) = SMALLK_CASES[case]
+    if kind == "lo":
+        first = list(range(cnt))
+    elif kind == "hi":
+        first = list(range(n - cnt, n))
+    else:
+        first = sorted(int(q) for q in np.random.Generator(np.random.PCG64(7)).permutation(n)[:cnt])
+    rest = [q for q in range(n) if q not in first]
+    return tensors.pseudo_physical_network(n, edges, [first, rest], seed)
+
+
 def planner_network(seed: int, kind: str = "g30"):
     """Timing-only networks for the learned planner (Gaussian FP32 values):
     ``g30`` -- 27-30 qubits, 4-6 subcircuits, m+5..m+7 cuts, widths <= 11
