@@ -800,7 +800,7 @@ tqc_status build_batch(Plan *const *plans, void *const *outs, int n, Batch *b) {
             level_of[sp.c] = lvl;
             EpiTables tb;
             // staged write-out of the CUDA-core tiles (64 x 64 row-major, or the small-K form's)
-            if (bs.smallk) host_tables(&tb, bs.a.epi, bs.sk.rowmajor != 0, bs.sk.pitch);
+            if (bs.smallk) host_tables(&tb, bs.a.epi, true, 0);  // the gather's element offsets
             else host_tables(&tb, bs.a.epi, true, 68);
             const int si = (int)steps.size();
             steps.push_back(bs);

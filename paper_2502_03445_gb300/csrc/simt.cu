@@ -102,12 +102,11 @@ __global__ void __launch_bounds__(128, (QM == 1) == RM ? 8 : 6)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     EpiTables *tb = (EpiTables *)smem_raw;
     float *buf = (float *)(smem_raw + sizeof(EpiTables));
-    if (!L.direct) {
-        epi_tables_init(tb, args.epi, RM, L.pitch, threadIdx.x, 128);
+    if (!L.direct) {  // the gather's element offsets (its staging offsets are unused)
+        epi_tables_init(tb, args.epi, true, 0, threadIdx.x, 128);
         __syncthreads();
     }
-    smallk_tiles_body<KB, QM, RM, false>(args, tb, L.direct, L.pitch, L.gmode, col_tiles, blockIdx.x, n_tiles,
-                                         gridDim.x, buf, threadIdx.x, 1);
+    smallk_tiles_body<KB, QM, RM, false>(args, tb, L, col_tiles, blockIdx.x, n_tiles, gridDim.x, buf, threadIdx.x, 1);
 }
 
 // FP64 twin for the scalar total-mass network (small; one config).
@@ -304,8 +303,8 @@ bool smallk_ok(int mb, int nb, int kb, bool kblk) {
 }
 
 // Start from 64 x 64, grow the side the step still has until the tile holds
-// 2^12 results, then shrink the larger side until operands and staging (in
-// either orientation) fit SMALLK_BYTES.
+// 2^12 results, then shrink the larger side until operands and staging fit
+// SMALLK_BYTES.
 TileShape smallk_tile(int mb, int nb, int kb) {
     int a = std::min(mb, 6), b = std::min(nb, 6);
     while (a + b < 12 && (a < mb || b < nb)) {
@@ -313,8 +312,7 @@ TileShape smallk_tile(int mb, int nb, int kb) {
         else ++b;
     }
     auto fits = [&](int x, int y) {
-        return smallk_op_bytes(x, y, kb) <= SMALLK_BYTES &&
-               std::max(smallk_stage_bytes(x, y, true), smallk_stage_bytes(x, y, false)) <= SMALLK_BYTES;
+        return smallk_op_bytes(x, y, kb) <= SMALLK_BYTES && smallk_stage_bytes(x, y) <= SMALLK_BYTES;
     };
     while (!fits(a, b) && (a > 2 || b > 2)) {
         if (a >= b && a > 2) --a;
@@ -336,7 +334,8 @@ static uint64_t host_pdep64(uint64_t src, uint64_t mask) {
 
 // Direct stores when the result's lowest four or more bits are bits of one
 // tile dimension and at least two lanes run along it (whole 32-byte sectors
-// per warp store), else staging in the orientation pick_staging chooses.
+// per warp store), else the tile staged in destination order with the lanes
+// along the dimension that has more of the tile's seven lowest result bits.
 SmallkLayout smallk_layout(const EpiParams &e) {
     SmallkLayout L;
     const uint64_t mR = host_pdep64(e.lowRc, e.tileMask), mC = host_pdep64(e.lowCc, e.tileMask);
@@ -352,10 +351,12 @@ SmallkLayout smallk_layout(const EpiParams &e) {
         const int qm = qm_for(rm);
         return rm ? b - 2 - (2 - qm) : a - 2 - (qm - 1);
     };
-    const StagePick pk = pick_staging(e.lowRc, e.lowCc);
-    L.rowmajor = pk.rowmajor;
-    L.gmode = pk.gmode;
-    L.pitch = pk.rowmajor ? (1 << b) + 4 : (1 << a) + 4;
+    // bit of t holding the n-th lowest bit of a compact mask
+    auto nth = [](uint32_t m, int n) {
+        for (int i = 0; i < n; ++i) m &= m - 1;
+        return (uint32_t)__builtin_ctz(m);
+    };
+    L.rowmajor = pick_staging(e.lowRc, e.lowCc).rowmajor;
     L.direct = 0;
     if (run(mC) >= 4 && lanes(1) >= 1) {
         L.direct = 1;
@@ -365,6 +366,12 @@ SmallkLayout smallk_layout(const EpiParams &e) {
         L.rowmajor = 0;
     }
     L.qm = qm_for(L.rowmajor);
+    L.pr0 = nth(e.lowRc, 0);
+    L.pr1 = nth(e.lowRc, 1);
+    L.pc0 = nth(e.lowCc, 0);
+    L.pc1 = nth(e.lowCc, 1);
+    const bool r0 = e.lowRc & 1u, r1 = e.lowRc & 2u;
+    L.pat = (r0 && r1) ? 0 : (!r0 && !r1) ? 1 : (r0 ? 2 : 3);
     return L;
 }
 
@@ -372,9 +379,10 @@ cudaError_t launch_smallk(const StepArgs &a, cudaStream_t s) {
     const EpiParams &e = a.epi;
     if (!smallk_ok(a.mb, a.nb, a.kb, a.kblk != 0) || e.a_bits < 2 || e.b_bits < 2 || a.ksplit != 1)
         return cudaErrorInvalidValue;
+    if (e.L < 2) return cudaErrorInvalidValue;  // the result's two lowest bits lie in every tile
     const SmallkLayout L = smallk_layout(e);
     const int bytes = std::max(smallk_op_bytes(e.a_bits, e.b_bits, a.kb),
-                               L.direct ? 0 : smallk_stage_bytes(e.a_bits, e.b_bits, L.rowmajor != 0));
+                               L.direct ? 0 : smallk_stage_bytes(e.a_bits, e.b_bits));
     if (bytes > SMALLK_BYTES) return cudaErrorInvalidValue;
     const size_t smem = sizeof(EpiTables) + (size_t)bytes;
     const int64_t col_tiles = 1ll << (a.nb - e.b_bits);

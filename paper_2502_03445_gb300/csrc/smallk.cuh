@@ -9,10 +9,10 @@
 // result layout, so that the rows (and columns) it reads are contiguous
 // operand memory, loaded with 16-byte loads and stored transposed ([k][row],
 // [k][col]) in shared memory.  Every thread then forms 4 x 8 (or 8 x 4)
-// results as outer products of float4 quads, the tile is staged in the
-// orientation that makes the destination-order gather conflict-free, and
-// the staged tile is written with runs of consecutive addresses
-// (epi_readout).  The staging buffer aliases the operand buffer.
+// results as outer products of float4 quads and writes them to HBM straight
+// from registers when the layout allows, else through a staged copy of the
+// tile in destination order, gathered 16 bytes at a time (SmallkLayout).
+// The staging buffer aliases the operand buffer.
 #pragma once
 
 #include "device_common.cuh"
@@ -20,27 +20,39 @@
 
 namespace tqc {
 
-// Shared memory a small-K tile uses (operands and staging alias).
+// Shared memory of a small-K tile: its operands, or its staged results
+// (which alias them).
 constexpr int SMALLK_BYTES = 34816;
 
 __host__ __device__ inline int smallk_op_bytes(int a, int b, int kb) {
     return (1 << kb) * ((1 << a) + 4 + (1 << b) + 4) * 4;
 }
-__host__ __device__ inline int smallk_stage_bytes(int a, int b, bool rowmajor) {
-    return rowmajor ? (1 << a) * ((1 << b) + 4) * 4 : (1 << b) * ((1 << a) + 4) * 4;
-}
+// The staged tile: 2^(a+b) floats in the tile's destination order.
+__host__ __device__ inline int smallk_stage_bytes(int a, int b) { return 4 << (a + b); }
 
 // How a small-K step writes its tiles.  direct: the result's lowest bits
 // (at least four) are bits of one dimension of the tile, so each thread's
 // float4 quads along that dimension are 16 contiguous bytes and the lanes
 // of a warp run along it: results go from registers straight to their
-// destination, with no staging.  Otherwise the tile is staged (rowmajor,
-// pitch) and gathered in destination order (gmode).  rowmajor also says
-// which dimension the lanes run along: columns when set.  qm: row quads per
-// thread (1: 4 x 8 results, 2: 8 x 4), 2 when the lanes run along rows.
+// destination, with no staging.  Otherwise the tile is staged in its own
+// destination order: element t of the tile (t = the tile's result bits,
+// compacted, lowest first) at word 4 swz(t >> 2) + (t & 3), swz an XOR of
+// the 16-byte chunk index that spreads the chunks of a warp's writes over
+// the banks.  The two lowest bits of t are two of the four lowest bits of
+// the tile's rows and columns, so every aligned four results of the
+// destination lie in one thread's 4 x 4 block: the thread writes them as
+// one float4 and the gather reads 16 bytes per four results, for any
+// layout.  pat says which: 0 rows 0, 1; 1 columns 0, 1; 2 row 0 then column
+// 0; 3 column 0 then row 0.  pr0 / pr1 / pc0 / pc1: the bit of t holding
+// row bit 0 / 1 and column bit 0 / 1.  rowmajor says which dimension the
+// lanes run along (columns when set); qm: row quads per thread (1: 4 x 8
+// results, 2: 8 x 4), 2 when the lanes run along rows.
 struct SmallkLayout {
-    int direct, rowmajor, pitch, gmode, qm;
+    int direct, rowmajor, qm, pat;
+    uint32_t pr0, pr1, pc0, pc1;
 };
+
+__device__ __forceinline__ uint32_t sk_swz(uint32_t q) { return q ^ (((q >> 3) ^ (q >> 6) ^ (q >> 9)) & 7u); }
 
 // The layout of a step with these epilogue parameters (host; simt.cu).
 SmallkLayout smallk_layout(const EpiParams &e);
@@ -86,13 +98,78 @@ __device__ __forceinline__ void sk_direct_store(const EpiParams &e, const float 
     }
 }
 
+// Stage a thread's 4 QM x 4 QN results in the tile's destination order (the
+// layout above).  trq[u] / tcq[v]: the bits of t of the thread's row quad u /
+// column quad v (their rows 0..3 / columns 0..3 add the bits pr0, pr1 /
+// pc0, pc1).
+template <int QM, int QN>
+__device__ __forceinline__ void sk_stage(float *stg, const float (&acc)[4 * QM][4 * QN], const SmallkLayout &L,
+                                         const uint64_t (&trq)[QM], const uint64_t (&tcq)[QN]) {
+    auto put = [&](uint32_t t, float x0, float x1, float x2, float x3) {
+        *(float4 *)(stg + (sk_swz(t >> 2) << 2)) = make_float4(x0, x1, x2, x3);
+    };
+    const uint32_t R0 = 1u << L.pr0, R1 = 1u << L.pr1, C0 = 1u << L.pc0, C1 = 1u << L.pc1;
+#pragma unroll
+    for (int u = 0; u < QM; ++u)
+#pragma unroll
+        for (int v = 0; v < QN; ++v) {
+            const uint32_t t0 = (uint32_t)(trq[u] | tcq[v]);
+            const int r = 4 * u, c = 4 * v;
+            if (L.pat == 0) {  // rows 0..3 of one column
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    put(t0 | ((j & 1) ? C0 : 0u) | ((j & 2) ? C1 : 0u), acc[r][c + j], acc[r + 1][c + j],
+                        acc[r + 2][c + j], acc[r + 3][c + j]);
+            } else if (L.pat == 1) {  // columns 0..3 of one row
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+                    put(t0 | ((i & 1) ? R0 : 0u) | ((i & 2) ? R1 : 0u), acc[r + i][c], acc[r + i][c + 1],
+                        acc[r + i][c + 2], acc[r + i][c + 3]);
+            } else {  // 2 x 2 blocks: (row 0, column 0) or (column 0, row 0) lowest
+#pragma unroll
+                for (int i = 0; i < 4; i += 2)
+#pragma unroll
+                    for (int j = 0; j < 4; j += 2) {
+                        const uint32_t t = t0 | (i ? R1 : 0u) | (j ? C1 : 0u);
+                        if (L.pat == 2)
+                            put(t, acc[r + i][c + j], acc[r + i + 1][c + j], acc[r + i][c + j + 1],
+                                acc[r + i + 1][c + j + 1]);
+                        else
+                            put(t, acc[r + i][c + j], acc[r + i][c + j + 1], acc[r + i + 1][c + j],
+                                acc[r + i + 1][c + j + 1]);
+                    }
+            }
+        }
+}
+
+// Write the staged tile (E results) to the destination: thread gt takes
+// the aligned fours t = 4 gt + 512 n; element offset of t = g_hi[t >> 7] +
+// g_lo[t & 127] (t & 127 fixed per thread).  MODE: the output mode, or -1
+// to dispatch it per store (fewer live registers).
+template <int MODE>
+__device__ __forceinline__ void sk_gather(const EpiTables *tb, const float *stg, const EpiParams &e, uint64_t base,
+                                          int E, int gt) {
+    const int mode = MODE >= 0 ? MODE : e.mode;
+    const double sd = (mode == EPI_OUT_F32 || mode == EPI_OUT_F64) ? e.zinfo[1] : 1.0;
+    const float sf = (float)sd;
+    const uint64_t gb = base + tb->g_lo[(gt * 4) & 127];
+#pragma unroll 4
+    for (int t = gt * 4; t < E; t += 512) {
+        const float4 q = *(const float4 *)(stg + (sk_swz((uint32_t)t >> 2) << 2));
+        const float v[4] = {q.x, q.y, q.z, q.w};
+        if constexpr (MODE >= 0) store_vals<MODE, 4>(e, gb + tb->g_hi[t >> 7], v, sf, sd);
+        else store_run_f32(e, gb + tb->g_hi[t >> 7], v, 4, sd);
+    }
+}
+
 __device__ __forceinline__ void sk_bar(int id) { asm volatile("bar.sync %0, 128;" ::"r"(id) : "memory"); }
 
 // Tiles t0, t0 + stride, ... < t_end of a small-K step (col_tiles: a power
 // of two).  KB = log2 K; QM x QN float4 quads per thread (1 x 2 or 2 x 1);
-// RM: the lanes run along columns (a staging buffer is row-major).  gt: the thread's index in the group, bid: the group's named
-// barrier; pitch / gmode: the staging pitch and gather mode the tables `tb`
-// were built for.  Every thread's place in the tile is fixed across tiles.
+// RM: the lanes run along columns.  gt: the thread's index in the group,
+// bid: the group's named barrier; tb: the step's element-offset tables (the
+// staged form's gather).  Every thread's place in the tile is fixed across
+// tiles.
 // The tile's row / column block and its base element advance by masked
 // additions instead of a division and two bit deposits per tile: with every
 // bit outside mask M set, pdep(x, M) + pdep(d, M) carries across the gaps,
@@ -103,9 +180,10 @@ __device__ __forceinline__ void sk_bar(int id) { asm volatile("bar.sync %0, 128;
 // tile and the output mode dispatched per store, which keep fewer values
 // live.
 template <int KB, int QM, bool RM, bool LEAN>
-__device__ __forceinline__ void smallk_tiles_body(const StepArgs &sa, const EpiTables *tb, int direct, int pitch,
-                                                  int gmode, int64_t col_tiles, int64_t t0, int64_t t_end,
-                                                  int64_t stride, float *buf, int gt, int bid) {
+__device__ __forceinline__ void smallk_tiles_body(const StepArgs &sa, const EpiTables *tb, const SmallkLayout L,
+                                                  int64_t col_tiles, int64_t t0, int64_t t_end, int64_t stride,
+                                                  float *buf, int gt, int bid) {
+    const int direct = L.direct;
     constexpr int K = 1 << KB;
     constexpr int QN = 3 - QM;
     if (t0 >= t_end) return;
@@ -116,6 +194,7 @@ __device__ __forceinline__ void smallk_tiles_body(const StepArgs &sa, const EpiT
     const int Me = 1 << a, Ne = 1 << b;
     const int PA = Me + 4, PB = Ne + 4;
     float *As = buf, *Bs = buf + K * PA;
+    float *const stg = buf;  // aliases the operands, read before it is written
     // thread (tx, ty) owns row quads ty + Y u and column quads tx + X v; the
     // lanes of a warp run along the staging buffer's contiguous dimension
     // (columns when it is row-major), so that its float4 writes are
@@ -133,13 +212,12 @@ __device__ __forceinline__ void smallk_tiles_body(const StepArgs &sa, const EpiT
     // of each row quad and first column of each column quad; the rows and
     // columns within a quad follow by masked increments
     const uint64_t mR = pdep64(e.lowRc, e.tileMask), mC = pdep64(e.lowCc, e.tileMask);
+    // (staged form: the same arrays hold the bits of t of the thread's quads)
     uint64_t gr[QM], gc[QN];
-    if (direct) {
 #pragma unroll
-        for (int u = 0; u < QM; ++u) gr[u] = pdep64((uint64_t)oa[u], mR);
+    for (int u = 0; u < QM; ++u) gr[u] = direct ? pdep64((uint64_t)oa[u], mR) : pdep32((uint32_t)oa[u], e.lowRc);
 #pragma unroll
-        for (int v = 0; v < QN; ++v) gc[v] = pdep64((uint64_t)ob[v], mC);
-    }
+    for (int v = 0; v < QN; ++v) gc[v] = direct ? pdep64((uint64_t)ob[v], mC) : pdep32((uint32_t)ob[v], e.lowCc);
     // tile counts fit 32 bits (2^31 tiles of 2^12 results would be 2^43 results)
     const int lct = __ffsll((long long)col_tiles) - 1;
     const int cmask = (int)col_tiles - 1;
@@ -234,39 +312,30 @@ __device__ __forceinline__ void smallk_tiles_body(const StepArgs &sa, const EpiT
                 }
 #undef TQC_SK_DIRECT
             }
-            if constexpr (!LEAN) {
-                const int c2 = ct + sc;
-                const int carry = c2 >> lct;
-                ct = c2 & cmask;
-                rt += sr + carry;
-                pc = ((pc | ~e.highC) + dc) & e.highC;
-                pr = ((pr | ~e.highR) + (carry ? dr1 : dr0)) & e.highR;
-            }
-            continue;
-        }
-        float *stg = buf;
-        if (active) {
-#pragma unroll
-            for (int u = 0; u < QM; ++u)
-#pragma unroll
-                for (int v = 0; v < QN; ++v) {
-                    float *d = RM ? stg + oa[u] * pitch + ob[v] : stg + ob[v] * pitch + oa[u];
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        if constexpr (RM)
-                            *(float4 *)(d + i * pitch) = make_float4(acc[4 * u + i][4 * v], acc[4 * u + i][4 * v + 1],
-                                                                     acc[4 * u + i][4 * v + 2], acc[4 * u + i][4 * v + 3]);
-                        else
-                            *(float4 *)(d + i * pitch) = make_float4(acc[4 * u][4 * v + i], acc[4 * u + 1][4 * v + i],
-                                                                     acc[4 * u + 2][4 * v + i], acc[4 * u + 3][4 * v + i]);
-                    }
-                }
-        }
-        sk_bar(bid);
-        if constexpr (LEAN) {
-            epi_readout_rt(tb, stg, e, base, Me * Ne, gt, 128, gmode);
         } else {
-            epi_readout(tb, stg, e, base, Me * Ne, gt, 128, gmode);
+            if (active) sk_stage<QM, QN>(stg, acc, L, gr, gc);
+            sk_bar(bid);
+            if constexpr (LEAN) {
+                sk_gather<-1>(tb, stg, e, base, Me * Ne, gt);
+            } else {
+#define TQC_SK_GATHER(M) \
+    case M: sk_gather<M>(tb, stg, e, base, Me * Ne, gt); break;
+                switch (e.mode) {
+                    TQC_SK_GATHER(EPI_F32)
+                    TQC_SK_GATHER(EPI_TF32)
+                    TQC_SK_GATHER(EPI_BF16)
+                    TQC_SK_GATHER(EPI_BF16X2)
+                    TQC_SK_GATHER(EPI_F64_SET)
+                    TQC_SK_GATHER(EPI_F64_ADD)
+                    TQC_SK_GATHER(EPI_OUT_F32)
+                    TQC_SK_GATHER(EPI_OUT_F64)
+                    default: break;
+                }
+#undef TQC_SK_GATHER
+            }
+            sk_bar(bid);  // the next tile's operands overwrite the staging buffer
+        }
+        if constexpr (!LEAN) {
             const int c2 = ct + sc;
             const int carry = c2 >> lct;
             ct = c2 & cmask;
@@ -274,26 +343,22 @@ __device__ __forceinline__ void smallk_tiles_body(const StepArgs &sa, const EpiT
             pc = ((pc | ~e.highC) + dc) & e.highC;
             pr = ((pr | ~e.highR) + (carry ? dr1 : dr0)) & e.highR;
         }
-        sk_bar(bid);  // the next tile's operands overwrite the staging buffer
     }
 }
 
 template <int KB, int QM, bool RM>
-__device__ __noinline__ void smallk_tiles_lean(const StepArgs &sa, const EpiTables *tb, int direct, int pitch,
-                                               int gmode, int64_t col_tiles, int64_t t0, int64_t t_end,
-                                               int64_t stride, float *buf, int gt, int bid) {
-    smallk_tiles_body<KB, QM, RM, true>(sa, tb, direct, pitch, gmode, col_tiles, t0, t_end, stride, buf, gt, bid);
+__device__ __noinline__ void smallk_tiles_lean(const StepArgs &sa, const EpiTables *tb, const SmallkLayout L,
+                                               int64_t col_tiles, int64_t t0, int64_t t_end, int64_t stride,
+                                               float *buf, int gt, int bid) {
+    smallk_tiles_body<KB, QM, RM, true>(sa, tb, L, col_tiles, t0, t_end, stride, buf, gt, bid);
 }
 
 template <int KB, int QM, bool RM, bool LEAN>
 __device__ __forceinline__ void smallk_tiles(const StepArgs &sa, const EpiTables *tb, const SmallkLayout &L,
                                              int64_t col_tiles, int64_t t0, int64_t t_end, int64_t stride, float *buf,
                                              int gt, int bid) {
-    if constexpr (LEAN)
-        smallk_tiles_lean<KB, QM, RM>(sa, tb, L.direct, L.pitch, L.gmode, col_tiles, t0, t_end, stride, buf, gt, bid);
-    else
-        smallk_tiles_body<KB, QM, RM, false>(sa, tb, L.direct, L.pitch, L.gmode, col_tiles, t0, t_end, stride, buf, gt,
-                                             bid);
+    if constexpr (LEAN) smallk_tiles_lean<KB, QM, RM>(sa, tb, L, col_tiles, t0, t_end, stride, buf, gt, bid);
+    else smallk_tiles_body<KB, QM, RM, false>(sa, tb, L, col_tiles, t0, t_end, stride, buf, gt, bid);
 }
 
 // The instance for the step's K, tile width and staging orientation.
