@@ -207,10 +207,10 @@ __device__ void ingest_range(const BIngest &it, int tid, int nt) {
             case ST_F32: ((float *)g.dst)[d] = v; break;
             case ST_TF32: ((float *)g.dst)[d] = to_tf32(v); break;
             case ST_BF16: ((__nv_bfloat16 *)g.dst)[d] = __float2bfloat16_rn(v); break;
-            case ST_BF16X2: {
-                __nv_bfloat16 h = __float2bfloat16_rn(v);
+            case ST_BF16X2: {  // the standalone ingest's split, from the FP32 value
+                const __nv_bfloat16 h = __float2bfloat16_rn(v);
                 ((__nv_bfloat16 *)g.dst)[d] = h;
-                ((__nv_bfloat16 *)g.dst_lo)[d] = __float2bfloat16_rn((float)(v64 - (double)__bfloat162float(h)));
+                ((__nv_bfloat16 *)g.dst_lo)[d] = __float2bfloat16_rn(v - __bfloat162float(h));
             } break;
             default: break;
         }

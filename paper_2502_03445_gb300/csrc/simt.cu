@@ -193,17 +193,18 @@ __global__ void ingest_kernel(IngestArgs g, int64_t n_dst) {
             else ((float *)g.dst)[d] = (float)v;
             continue;
         }
-        float v = ld_src<float>(g.src, g.src_dtype, s);
+        const float v = ld_src<float>(g.src, g.src_dtype, s);
         switch (g.storage) {
             case ST_F32: ((float *)g.dst)[d] = v; break;
             case ST_TF32: ((float *)g.dst)[d] = to_tf32(v); break;
             case ST_BF16: ((__nv_bfloat16 *)g.dst)[d] = __float2bfloat16_rn(v); break;
             case ST_BF16X2: {
-                // split from the FP64 source so the lo plane carries the FP32 remainder
-                double v64 = ld_src<double>(g.src, g.src_dtype, s);
-                __nv_bfloat16 h = __float2bfloat16_rn((float)v64);
+                // hi = bf16(v), lo = bf16(v - hi) from the FP32 value (v - hi is
+                // exact in FP32); one FP64 conversion per element, which matters
+                // on a part whose FP64 rate is a small fraction of its FP32 rate
+                const __nv_bfloat16 h = __float2bfloat16_rn(v);
                 ((__nv_bfloat16 *)g.dst)[d] = h;
-                ((__nv_bfloat16 *)g.dst_lo)[d] = __float2bfloat16_rn((float)(v64 - (double)__bfloat162float(h)));
+                ((__nv_bfloat16 *)g.dst_lo)[d] = __float2bfloat16_rn(v - __bfloat162float(h));
             } break;
             case ST_F64: ((double *)g.dst)[d] = ld_src<double>(g.src, g.src_dtype, s); break;
             default: break;
