@@ -277,8 +277,10 @@ TQC_API tqc_status tqc_contract_host(tqc_plan_t plan, const void *const *host_te
  * step tiles (CUDA-core and tcgen05), each waiting, with a bounded wait, on
  * the counters of the items that produce its operands.  A plan's steps from
  * its first large one on (predicted to take at least the threshold of
- * tqc_batch_tail_threshold) run after that kernel, on the same stream, as
- * the ordinary step kernels of tqc_contract.  d_outs[i] receives
+ * tqc_batch_tail_threshold) run after that kernel as the ordinary step
+ * kernels of tqc_contract, on four library-owned streams forked from
+ * cuda_stream and joined back to it before the call returns (so the call
+ * stays stream-ordered and capturable).  d_outs[i] receives
  * plan i's bin (FP32, renormalised with the plan's cached total mass).
  * Requirements: every plan was contracted once since its tensors last
  * changed, and none is sliced (TQC_ERR_UNSUPPORTED otherwise).  The first

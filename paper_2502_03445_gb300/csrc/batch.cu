@@ -645,9 +645,17 @@ struct BatchTail {
     void *out;
 };
 
+// The large steps of different plans are independent: they run on a few
+// streams forked from the caller's (and joined back before the call
+// returns), so one plan's last wave and the gaps between launches overlap
+// another plan's steps.  Plans are spread by their predicted time, longest
+// first onto the least loaded stream.
+constexpr int TAIL_STREAMS = 4;
+
 struct Batch {
     std::vector<const void *> key;
     std::vector<BatchTail> tails;
+    std::vector<int> tail_stream;  // stream of each tail
     BItem *d_items = nullptr;
     BStep *d_steps = nullptr;
     EpiTables *d_tables = nullptr;
@@ -670,6 +678,12 @@ std::mutex g_batch_mu;
 Batch g_batch;
 int g_inject_stall = 0;
 double g_tail_s = 16e-6;
+// process-wide, created on first use (the tail streams of every device's
+// batches; streams and events are per device, so they are created for the
+// device current at first use)
+cudaStream_t g_tail_ts[TAIL_STREAMS] = {};
+cudaEvent_t g_tail_fork = nullptr, g_tail_join[TAIL_STREAMS] = {};
+int g_tail_device = -1;
 
 template <typename T>
 cudaError_t upload(T **dst, const std::vector<T> &v) {
@@ -683,6 +697,7 @@ cudaError_t upload(T **dst, const std::vector<T> &v) {
 }
 
 tqc_status build_batch(Plan *const *plans, void *const *outs, int n, Batch *b) {
+    std::vector<double> tail_time;  // predicted seconds of each plan's large steps
     std::vector<BItem> items;
     std::vector<BStep> steps;
     std::vector<EpiTables> tables;
@@ -739,7 +754,15 @@ tqc_status build_batch(Plan *const *plans, void *const *outs, int n, Batch *b) {
             }
         }
         if (first_tail < p.steps.size() && first_tail > 0 && p.steps[first_tail].fuse == 2) --first_tail;
-        if (first_tail < p.steps.size()) b->tails.push_back(BatchTail{&p, first_tail, outs[pi]});
+        if (first_tail < p.steps.size()) {
+            b->tails.push_back(BatchTail{&p, first_tail, outs[pi]});
+            double t = 0;
+            for (size_t i = first_tail; i < p.steps.size(); ++i) {
+                const StepPlan &sp = p.steps[i];
+                t += step_cost(sp.mb, sp.nb, sp.kb, sp.klass, sp.prec, cc).time_s;
+            }
+            tail_time.push_back(t);
+        }
         for (size_t si0 = 0; si0 < first_tail; ++si0) {
             const StepPlan &sp = p.steps[si0];
             BStep bs;
@@ -809,6 +832,18 @@ tqc_status build_batch(Plan *const *plans, void *const *outs, int n, Batch *b) {
                 leveled.push_back({lvl, BItem{IT_STEP, si, t, std::min(per_item, n_tiles - t)}});
         }
     }
+    {
+        std::vector<size_t> order(tail_time.size());
+        for (size_t i = 0; i < order.size(); ++i) order[i] = i;
+        std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) { return tail_time[x] > tail_time[y]; });
+        double load[TAIL_STREAMS] = {0};
+        b->tail_stream.assign(tail_time.size(), 0);
+        for (size_t i : order) {
+            const int k = (int)(std::min_element(load, load + TAIL_STREAMS) - load);
+            b->tail_stream[i] = k;
+            load[k] += tail_time[i];
+        }
+    }
     if (g_inject_stall) leveled.insert(leveled.begin(), {0, BItem{IT_STALL, n_counters++, 0, 0}});
     std::stable_sort(leveled.begin(), leveled.end(), [](auto &x, auto &y) { return x.first < y.first; });
     for (auto &li : leveled) items.push_back(li.second);
@@ -875,11 +910,35 @@ tqc_status tqc_contract_batch(const tqc_plan_t *plans, void *const *d_outs, int3
                                         g_batch.d_err);
     e = cudaGetLastError();
     if (e != cudaSuccess) return fail(TQC_ERR_CUDA, std::string("batch launch: ") + cudaGetErrorString(e));
-    for (const BatchTail &t : g_batch.tails) {
-        tqc_status st = exec_run_tail(*t.p, t.first, t.out, cuda_stream);
-        if (st != TQC_OK) return st;
+    if (g_batch.tails.empty()) return TQC_OK;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (g_tail_device != dev) {
+        if (g_tail_device >= 0) return fail(TQC_ERR_UNSUPPORTED, "batched launches on a second device");
+        for (int k = 0; k < TAIL_STREAMS && e == cudaSuccess; ++k) {
+            e = cudaStreamCreateWithFlags(&g_tail_ts[k], cudaStreamNonBlocking);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g_tail_join[k], cudaEventDisableTiming);
+        }
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g_tail_fork, cudaEventDisableTiming);
+        if (e != cudaSuccess) return fail(TQC_ERR_CUDA, std::string("batch tail streams: ") + cudaGetErrorString(e));
+        g_tail_device = dev;
     }
-    return TQC_OK;
+    // fork: every tail stream waits for the persistent kernel
+    e = cudaEventRecord(g_tail_fork, s);
+    for (int k = 0; k < TAIL_STREAMS && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(g_tail_ts[k], g_tail_fork, 0);
+    if (e != cudaSuccess) return fail(TQC_ERR_CUDA, std::string("batch fork: ") + cudaGetErrorString(e));
+    tqc_status st = TQC_OK;
+    for (size_t i = 0; i < g_batch.tails.size() && st == TQC_OK; ++i) {
+        const BatchTail &t = g_batch.tails[i];
+        st = exec_run_tail(*t.p, t.first, t.out, g_tail_ts[g_batch.tail_stream[i]]);
+    }
+    // join (also after a failed launch, so the caller's stream stays ordered)
+    for (int k = 0; k < TAIL_STREAMS; ++k) {
+        cudaError_t ej = cudaEventRecord(g_tail_join[k], g_tail_ts[k]);
+        if (ej == cudaSuccess) ej = cudaStreamWaitEvent(s, g_tail_join[k], 0);
+        if (ej != cudaSuccess && st == TQC_OK) st = fail(TQC_ERR_CUDA, std::string("batch join: ") + cudaGetErrorString(ej));
+    }
+    return st;
 }
 
 tqc_status tqc_batch_status(void *cuda_stream) {
