@@ -178,14 +178,19 @@ def smallk_network(case: str, seed: int = 1) -> Network:
 def planner_network(seed: int, kind: str = "g30"):
     """Timing-only networks for the learned planner (Gaussian FP32 values):
     ``g30`` -- 27-30 qubits, 4-6 subcircuits, m+5..m+7 cuts, widths <= 11
-    (the 30-qubit grid workload's neighbourhood: sub-millisecond plans whose
-    kernel classes the analytic model ranks least well); ``small`` -- 20-24
-    qubits, 5-7 subcircuits, m+2..m+6 cuts, widths <= 12."""
+    (the 30-qubit grid workload's neighbourhood: sub-millisecond plans);
+    ``m9`` -- 24-27 qubits, 9-12 subcircuits, m+2..m+4 cuts, widths <= 10
+    (more subcircuits than TQC_PLANNER_AUTO plans exhaustively); ``small`` --
+    20-24 qubits, 5-7 subcircuits, m+2..m+6 cuts, widths <= 12."""
     rng = np.random.Generator(np.random.PCG64(seed))
     if kind == "g30":
         n, m = int(rng.integers(27, 31)), int(rng.integers(4, 7))
         cuts = int(rng.integers(m + 5, m + 8))
         return tensors.random_shape_network(n, m, cuts, 11, seed=seed, max_node_cuts=7)
+    if kind == "m9":
+        n, m = int(rng.integers(24, 28)), int(rng.integers(9, 13))
+        cuts = int(rng.integers(m + 2, m + 5))
+        return tensors.random_shape_network(n, m, cuts, 10, seed=seed, max_node_cuts=6)
     n, m = int(rng.integers(20, 25)), int(rng.integers(5, 8))
     cuts = int(rng.integers(m + 2, m + 7))
     return tensors.random_shape_network(n, m, cuts, 12, seed=seed, max_node_cuts=7)

@@ -82,7 +82,7 @@ enum {
     TQC_PLANNER_LEARNED = 2,     /* candidates within 10x of the best analytic estimate, ranked
                                     by log(analytic seconds) + the learned MLP's output (a model
                                     trained on log(measured / analytic seconds)) */
-    TQC_PLANNER_AUTO = 3         /* exhaustive for m <= 8, else greedy */
+    TQC_PLANNER_AUTO = 3         /* exhaustive for m <= 12, else greedy */
 };
 
 /* plan flags */
