@@ -183,9 +183,17 @@ __global__ void ingest_kernel(IngestArgs g, int64_t n_dst) {
         }
         return;
     }
-    for (int64_t d = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; d < n_dst; d += stride) {
-        int64_t s = g.src_base;
-        for (int b = 0; b < g.nbits; ++b)
+    // The grid is a power of two threads (2^lg): a thread's destination
+    // indices share their lg low bits, so their part of the source offset is
+    // summed once and each element adds only its bits from lg up.
+    const int lg = __ffsll((long long)stride) - 1;
+    const int64_t d0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t s_lo = g.src_base;
+    for (int b = 0; b < g.nbits && b < lg; ++b)
+        if (d0 >> b & 1) s_lo += 1ll << g.srcpos[b];
+    for (int64_t d = d0; d < n_dst; d += stride) {
+        int64_t s = s_lo;
+        for (int b = lg; b < g.nbits; ++b)
             if (d >> b & 1) s += 1ll << g.srcpos[b];
         if (g.scaled) {
             double v = ld_src<double>(g.src, g.src_dtype, s) * g.zinfo[1];
@@ -442,6 +450,8 @@ cudaError_t launch_ingest(const IngestArgs &g, int64_t n_dst, cudaStream_t s) {
     int64_t threads = g.reduce_bits > 0 ? n_dst * 32 : n_dst;
     int64_t blocks = std::min<int64_t>((threads + 255) / 256, (int64_t)sm_count() * 32);
     if (blocks < 1) blocks = 1;
+    // a power of two (the gather's stride; see ingest_kernel)
+    while (blocks & (blocks - 1)) blocks &= blocks - 1;
     ingest_kernel<<<(unsigned)blocks, 256, 0, s>>>(g, n_dst);
     return cudaGetLastError();
 }
