@@ -949,17 +949,18 @@ tqc_status tqc_batch_status(void *cuda_stream) {
     if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)cuda_stream);
     if (e != cudaSuccess) return fail(TQC_ERR_CUDA, std::string("batch status: ") + cudaGetErrorString(e));
     if (h) return fail(TQC_ERR_TIMEOUT, "a bounded wait in the batched launch gave up");
-    // the large steps' error words (their plans' own; cleared when read)
+    // the large steps' error words (their plans' own): every one that is set
+    // is cleared, so the next call reports only its own
+    bool timed_out = false;
     for (const BatchTail &t : g_batch.tails) {
         int w = 0;
         e = cudaMemcpyAsync(&w, t.p->d_zinfo + 2, sizeof(int), cudaMemcpyDeviceToHost, (cudaStream_t)cuda_stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)cuda_stream);
+        if (e == cudaSuccess && w) e = cudaMemsetAsync(t.p->d_zinfo + 2, 0, sizeof(int), (cudaStream_t)cuda_stream);
         if (e != cudaSuccess) return fail(TQC_ERR_CUDA, std::string("batch status: ") + cudaGetErrorString(e));
-        if (w) {
-            cudaMemsetAsync(t.p->d_zinfo + 2, 0, sizeof(int), (cudaStream_t)cuda_stream);
-            return fail(TQC_ERR_TIMEOUT, "a tensor-core step of the batch gave up waiting on its pipeline");
-        }
+        timed_out = timed_out || w != 0;
     }
+    if (timed_out) return fail(TQC_ERR_TIMEOUT, "a tensor-core step of the batch gave up waiting on its pipeline");
     return TQC_OK;
 }
 

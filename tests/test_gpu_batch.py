@@ -124,6 +124,33 @@ def test_batch_large_steps_after_the_persistent_kernel(tail_s):
         p.close()
 
 
+def test_batch_large_step_timeout_is_reported_once():
+    """With every step after the persistent kernel (threshold 0) and the
+    tensor-core step stall hook on, the large steps' bounded waits give up:
+    tqc_batch_status reports it and clears every plan's error word, and a
+    clean rerun reports nothing and matches the oracle."""
+    nets = uneven_networks()
+    hs, plans, outs, want = prepared(nets, ["auto"] * len(nets))
+    assert any(st["class"] == "tcgen05" for p in plans for st in p.describe()["steps"])
+    tqc.batch_tail_threshold(0.0)
+    try:
+        tqc.step_inject_stall(True)
+        try:
+            tqc.contract_batch(plans, outs)
+            with pytest.raises(tqc.TqcError) as ei:
+                tqc.batch_status()
+        finally:
+            tqc.step_inject_stall(False)
+        assert ei.value.status == tqc.ERR_TIMEOUT
+        tqc.contract_batch(plans, outs)
+        tqc.batch_status()
+        check(outs, want, plans)
+    finally:
+        tqc.batch_tail_threshold(16e-6)
+    for p in plans:
+        p.close()
+
+
 def test_batch_tail_threshold_rejects_negative():
     with pytest.raises(tqc.TqcError):
         tqc.batch_tail_threshold(-1.0)
