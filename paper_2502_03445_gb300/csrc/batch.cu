@@ -191,11 +191,19 @@ __device__ __forceinline__ void tmem_load16(uint32_t taddr, uint32_t (&r)[16]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// The elements it.lo + tid + k nt of an ingest chunk.  nt (512) is a power
+// of two and it.lo a multiple of it, so a thread's elements share their low
+// log2(nt) bits: that part of the source offset is summed once.
 __device__ void ingest_range(const BIngest &it, int tid, int nt) {
     const IngestArgs &g = it.g;
-    for (int64_t d = it.lo + tid; d < it.hi; d += nt) {
-        int64_t s = g.src_base;
-        for (int b = 0; b < g.nbits; ++b)
+    const int lg = __ffs(nt) - 1;
+    const int64_t d0 = it.lo + tid;
+    int64_t s_lo = g.src_base;
+    for (int b = 0; b < g.nbits && b < lg; ++b)
+        if (d0 >> b & 1) s_lo += 1ll << g.srcpos[b];
+    for (int64_t d = d0; d < it.hi; d += nt) {
+        int64_t s = s_lo;
+        for (int b = lg; b < g.nbits; ++b)
             if (d >> b & 1) s += 1ll << g.srcpos[b];
         const double v64 = g.src_dtype == TQC_F64 ? ((const double *)g.src)[s] : (double)((const float *)g.src)[s];
         if (g.scaled) {
