@@ -94,6 +94,48 @@ def test_exhaustive_never_worse_than_greedy():
         pe.close(), pg.close(), h.close()
 
 
+def test_auto_plans_exhaustively_up_to_12_subcircuits():
+    """TQC_PLANNER_AUTO takes the exhaustive DP for m <= 12 (its plan is the
+    DP's, never predicted slower than greedy's) and greedy above."""
+    for seed in range(9500, 9506):
+        net = workloads.planner_network(seed, "m9")
+        assert 9 <= len(net.nodes) <= 12
+        h = tqc.Network(net, shape_only=True)
+        pa = tqc.Plan(h, planner=tqc.PLANNER_AUTO)
+        pe = tqc.Plan(h, planner=tqc.PLANNER_EXHAUSTIVE)
+        pg = tqc.Plan(h, planner=tqc.PLANNER_GREEDY)
+        da, de, dg = pa.describe(), pe.describe(), pg.describe()
+        assert da["planner"] == "exhaustive"
+        assert da["predicted_s"] == de["predicted_s"] <= dg["predicted_s"] * (1 + 1e-12)
+        pa.close(), pe.close(), pg.close(), h.close()
+    net = tensors.random_shape_network(26, 13, 15, 10, seed=77, max_node_cuts=6)
+    h = tqc.Network(net, shape_only=True)
+    p = tqc.Plan(h, planner=tqc.PLANNER_AUTO)
+    assert p.describe()["planner"] == "greedy"
+    p.close(), h.close()
+
+
+def test_small_k_workload_cases_have_their_named_shapes():
+    """The small-K bench cases (gen.workloads.SMALLK_CASES) plan to a single
+    CUDA-core step of the named M, N, K, with the named bits lowest."""
+    for case in workloads.SMALLK_CASES:
+        m, rest = case.split("x")
+        n, k = rest.split("k")[0], rest.split("k")[1].split("_")[0]
+        net = workloads.smallk_network(case)
+        h = tqc.Network(net, shape_only=True)
+        p = tqc.Plan(h, precision="fp32")
+        (st,) = p.describe()["steps"]
+        assert (st["log2_m"], st["log2_n"], 1 << st["log2_k"]) == (int(m), int(n), int(k)), (case, st)
+        assert st["class"] == "simt"
+        if case.endswith("rows_low"):
+            assert st["mask_r"] & 0xF == 0xF
+        elif case.endswith("cols_low"):
+            assert st["mask_c"] & 0xF == 0xF
+        else:
+            assert st["mask_r"] & 0xF not in (0, 0xF)
+        p.close(), h.close()
+
+
 def test_slicing_under_budget():
     net = workloads.grid30()
     h = tqc.Network(net, shape_only=True)
