@@ -199,11 +199,13 @@ TQC_API tqc_status tqc_plan_step(tqc_plan_t plan, int32_t step, int32_t *log2_m,
  * Plan summary as JSON in buf (NUL-terminated, truncated to size).  Returns
  * the full length needed, excluding the NUL, or -1 on a bad handle.  Each
  * step lists its shape, class, precision, result layout, tile configuration
- * "ksplit" (K ranges run by separate CTAs, 1 = none) and "kblk" (1 = its
- * operands are stored K-blocked, [K / 64][rows][64], for rows over 64 KB;
- * fixed by the plan).  The first
- * contract sets tiles and splits (0 and 1 before it); the autotuner may
- * change them.
+ * ("tile": CUDA-core 0 = 64 x 64, 1 = 128 x 128, 2 = 128 x 64, 3 = the
+ * small-K tile; tcgen05 0 = 128 x 128, 1 = 128 x 64, 2 = 128 x 128 and
+ * 3 = 128 x 256 with the direct epilogue), "ksplit" (K ranges run by
+ * separate CTAs, 1 = none) and "kblk" (1 = its operands are stored
+ * K-blocked, [K / 64][rows][64], for rows over 64 KB; fixed by the plan).
+ * The first contract sets tiles and splits (0 and 1 before it); the
+ * autotuner may change them.
  */
 TQC_API int32_t tqc_plan_describe(tqc_plan_t plan, char *buf, int32_t size);
 
