@@ -7,10 +7,11 @@ fused multiply-adds as the general 64 x 64 .. 128 x 128 tiles, so the two
 must agree bit for bit (TQC_FLAG_NO_SMALLK selects the general tiles); both
 are checked against oracle C (the whole bin by FP64 pairwise contraction)
 at the FP32 gate.  The cases cover K = 1, 4 and 16, tiles of 8 and more
-columns (4 x 8 results per thread) and of 4 columns (8 x 4), both staging
-orientations and the gather modes of interleaved output bits, a final
-step, intermediates written as FP32 and as split-BF16 / TF32 operands of a
-tensor-core step, FP64 output, and the batched launch."""
+columns (4 x 8 results per thread) and of 4 columns (8 x 4), direct stores
+along rows and along columns, all four arrangements of the staged form's
+16-byte chunks (rows 0-1, columns 0-1, row then column, column then row
+lowest), a final step, intermediates written as FP32 and as split-BF16 /
+TF32 operands of a tensor-core step, FP64 output, and the batched launch."""
 import numpy as np
 import pytest
 
@@ -35,11 +36,14 @@ def _cuda():
 def _outs(n, groups):
     """Qubit lists of the subcircuits: `groups` is a list of (kind, count)
     with kind "hi" (the highest unused qubits), "lo" (the lowest), "even"
-    (every other unused qubit from the lowest) or "rest" (all unused)."""
+    (every other unused qubit from the lowest), "rest" (all unused) or
+    "set" (count: an explicit list)."""
     free = list(range(n))
     res = []
     for kind, cnt in groups:
-        if kind == "lo":
+        if kind == "set":
+            pick = list(cnt)
+        elif kind == "lo":
             pick = free[:cnt]
         elif kind == "hi":
             pick = free[-cnt:]
@@ -64,6 +68,11 @@ CASES = {
     # K = 1 (an outer product of two subcircuits without a shared cut), then K = 16
     "outer_product_then_k16": (17, [(0, 1), (1, 2)], [("lo", 6), ("even", 5), ("hi", 6)],
                                [[0, 2], [3, 1]], "fp32"),
+    # staged, the result's two lowest bits rows 0, 1 (row quads as float4 chunks)
+    "final_k4_staged_rows_lowest": (18, [(0, 1)], [("set", [0, 1] + list(range(4, 12))), ("rest", 8)], None, "fp32"),
+    # staged, column 0 then row 0 lowest (2 x 2 blocks as float4 chunks)
+    "final_k16_staged_col_then_row": (17, [(0, 1)] * 2, [("set", [1] + list(range(4, 13))), ("rest", 7)], None,
+                                      "fp32"),
     # a K = 16 intermediate feeding a tensor-core step (K = 64) as split-BF16 / TF32 operands
     "k16_into_tensor_core": (20, [(0, 1)] * 2 + [(1, 2)] * 3, [("hi", 8), ("even", 6), ("lo", 6)],
                              [[0, 1], [3, 2]], "auto"),
